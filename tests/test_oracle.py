@@ -1,0 +1,346 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each value comes from the
+paper's worked example, a closed form evaluated independently in mpmath,
+an invariant of orthogonal similarity, a known spectrum, LAPACK, or brute
+force on small inputs.
+"""
+import json
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+import pjac_inputs as pin
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+mpmath.mp.prec = 200
+
+
+def _ulps(x, ref):
+    return abs(x - ref) / (math.ulp(abs(ref)) if ref != 0 else math.ulp(0.0))
+
+
+def _mp_gap(aii, ajj, aij):
+    aii, ajj, aij = mpmath.mpf(aii), mpmath.mpf(ajj), mpmath.mpf(aij)
+    d = abs(aii - ajj)
+    return 2 * aij ** 2 / (d + mpmath.sqrt(d ** 2 + 4 * aij ** 2))
+
+
+def _mp_eig2(aii, ajj, aij):
+    aii, ajj, aij = mpmath.mpf(aii), mpmath.mpf(ajj), mpmath.mpf(aij)
+    m = (aii + ajj) / 2
+    r = mpmath.sqrt(((aii - ajj) / 2) ** 2 + aij ** 2)
+    return m - r, m + r
+
+
+# ---------------------------------------------------------------- Sec. 1 example
+def test_worked_example_pivots_and_scores():
+    g = json.load(open(os.path.join(GOLDEN, "worked_example.json")))
+    a = np.diag(g["A_diag"])
+    for i, j, v in g["A_offdiag"]:
+        a[i - 1, j - 1] = a[j - 1, i - 1] = v
+    assert np.array_equal(a, pin.worked_example())
+    rg = oracle.jacobi(a, pivot="greedy", select="brute", tol=1e-18, log_len=4)
+    rl = oracle.jacobi(a, pivot="gap", select="brute", tol=1e-18, log_len=4)
+    assert list(rg["pivots"][0] + 1) == g["greedy_first_pivot_1based"]
+    assert list(rl["pivots"][0] + 1) == g["gap_first_pivot_1based"]
+    l12 = oracle.gap_score(a[0, 0], a[1, 1], a[0, 1])
+    l34 = oracle.gap_score(a[2, 2], a[3, 3], a[2, 3])
+    assert l12 <= g["L12_at_most"] * (1 + g["L12_relative_slack"])
+    assert 0.1 * g["L34_order_of_magnitude"] < l34 < 10 * g["L34_order_of_magnitude"]
+    # both equal the Li--Li bound evaluated exactly at the stored FP64 entries
+    assert _ulps(l12, float(_mp_gap(a[0, 0], a[1, 1], a[0, 1]))) <= 4
+    assert _ulps(l34, float(_mp_gap(a[2, 2], a[3, 3], a[2, 3]))) <= 4
+    # after the first gap rotation the next pivot is (1,2); two rotations finish
+    assert [tuple(p) for p in rl["pivots"][:2]] == [(2, 3), (0, 1)]
+    assert rl["rotations"] == 2 and rg["rotations"] == 2
+
+
+# ---------------------------------------------------- Li--Li bound, 2x2 closed form
+def _random_triples(rng, count):
+    out = []
+    for _ in range(count):
+        s = 10.0 ** rng.uniform(-12, 3)
+        aii = rng.standard_normal() * s
+        ajj = aii + rng.standard_normal() * 10.0 ** rng.uniform(-14, 0) * s
+        aij = rng.standard_normal() * 10.0 ** rng.uniform(-10, 0) * s
+        out.append((aii, ajj, aij))
+    out += [(1.0, 1.0, 1e-9), (2.0, 1.0, 1e-8), (1.0, 2.0, -1e-8), (0.0, 0.0, 1.0),
+            (-3.0, 5.0, 0.25), (1e-300, 2e-300, 1e-301), (1e200, -1e200, 3e199)]
+    return out
+
+
+def test_gap_score_is_exact_2x2_eigenvalue_shift():
+    """Sec. 3: for the 2x2 block, L_ij equals the Li--Li bound, which for a
+    2x2 matrix is the exact distance from each diagonal entry to the nearer
+    eigenvalue."""
+    rng = np.random.default_rng(11)
+    for aii, ajj, aij in _random_triples(rng, 300):
+        l = oracle.gap_score(aii, ajj, aij)
+        lo, hi = _mp_eig2(aii, ajj, aij)
+        near = min(abs(hi - mpmath.mpf(max(aii, ajj))), abs(lo - mpmath.mpf(min(aii, ajj))))
+        assert _ulps(l, float(_mp_gap(aii, ajj, aij))) <= 6, (aii, ajj, aij)
+        assert abs(l - float(near)) <= 8 * math.ulp(float(near)) + 1e-300
+
+
+def test_gap_score_special_cases():
+    assert oracle.gap_score(1.0, 2.0, 0.0) == 0.0
+    assert oracle.gap_score(1.0, 1.0, 0.0) == 0.0
+    assert oracle.gap_score(3.0, 3.0, 0.5) == 0.5          # d = 0: L = |a_ij|
+    assert oracle.gap_score(1.0, 2.0, -1e-8) == oracle.gap_score(1.0, 2.0, 1e-8)
+    assert oracle.gap_score(2.0, 1.0, 1e-8) == oracle.gap_score(1.0, 2.0, 1e-8)
+    # homogeneous of degree one (exact powers of two keep every rounding)
+    for s in (2.0 ** 600, 2.0 ** -600, 2.0 ** 40):
+        assert oracle.gap_score(1.0 * s, 2.5 * s, 0.3 * s) == oracle.gap_score(1.0, 2.5, 0.3) * s
+    # greedy score
+    assert oracle.greedy_score(-3.5) == 3.5
+
+
+def test_rotation_diagonalises_2x2():
+    """Sec. 2: G_ij^T A_ij G_ij diagonal with G = [[c,-s],[s,c]]; the new
+    diagonal is the exact pair of eigenvalues, the larger staying with the
+    larger diagonal entry (|theta| <= pi/4)."""
+    rng = np.random.default_rng(5)
+    for aii, ajj, aij in _random_triples(rng, 300):
+        c, s, t = oracle.rotation(aii, ajj, aij)
+        assert abs(t) <= 1.0
+        C, S = mpmath.mpf(c), mpmath.mpf(s)
+        assert abs(C * C + S * S - 1) <= 6e-16
+        p, q, r = mpmath.mpf(aii), mpmath.mpf(aij), mpmath.mpf(ajj)
+        off = q * (C * C - S * S) + C * S * (r - p)     # (G^T A G)_12
+        scale = max(abs(aii), abs(ajj), abs(aij))
+        assert abs(off) <= 8e-16 * scale
+        a = np.array([[aii, aij, 0.0], [aij, ajj, 0.0], [0.0, 0.0, 7.0]])
+        oracle.rotate(a, 0, 1)
+        lo, hi = _mp_eig2(aii, ajj, aij)
+        big, small = (0, 1) if aii >= ajj else (1, 0)
+        assert abs(a[big, big] - float(hi)) <= 4 * math.ulp(float(hi)) + 4e-16 * scale
+        assert abs(a[small, small] - float(lo)) <= 4 * math.ulp(float(lo)) + 4e-16 * scale
+        assert a[0, 1] == 0.0 and a[1, 0] == 0.0
+
+
+def test_rotation_special_cases():
+    c, s, t = oracle.rotation(2.0, 2.0, 0.5)
+    assert t == 1.0 and abs(c - 2 ** -0.5) <= 2.3e-16 and s == c
+    c, s, t = oracle.rotation(2.0, 2.0, -0.5)     # zeta = -0 still takes sign +1
+    assert t == 1.0
+    c, s, t = oracle.rotation(1.0, 2.0, 0.0)
+    assert (c, s, t) == (1.0, 0.0, 0.0)
+    # sign of t: negative iff (a_ii - a_jj) * a_ij < 0
+    assert oracle.rotation(2.0, 1.0, 0.1)[2] > 0 and oracle.rotation(1.0, 2.0, 0.1)[2] < 0
+    assert oracle.rotation(2.0, 1.0, -0.1)[2] < 0 and oracle.rotation(1.0, 2.0, -0.1)[2] > 0
+
+
+def test_single_rotation_invariants():
+    """Orthogonal similarity preserves trace and ||A||_F; off(A)^2 drops by
+    exactly 2 a_ij^2 (Sec. 2, up to rounding); rows outside i,j keep the sum
+    of squares of their (k,i),(k,j) entries."""
+    rng = np.random.default_rng(3)
+    n = 9
+    b = rng.standard_normal((n, n))
+    a = b + b.T
+    for i, j in [(0, 1), (2, 7), (3, 8), (5, 6)]:
+        a0 = a.copy()
+        oracle.rotate(a, i, j)
+        assert abs(np.trace(a) - np.trace(a0)) <= 1e-13
+        assert abs(np.linalg.norm(a) - np.linalg.norm(a0)) <= 1e-13
+        off0 = np.sum(a0 ** 2) - np.sum(np.diag(a0) ** 2)
+        off1 = np.sum(a ** 2) - np.sum(np.diag(a) ** 2)
+        assert abs((off0 - off1) - 2 * a0[i, j] ** 2) <= 1e-12
+        for k in range(n):
+            if k in (i, j):
+                continue
+            assert abs(a[k, i] ** 2 + a[k, j] ** 2 - a0[k, i] ** 2 - a0[k, j] ** 2) <= 1e-13
+        assert np.array_equal(a, a.T)
+        # exact transform in mpmath: A' = G^T A G
+        c, s, _ = oracle.rotation(a0[i, i], a0[j, j], a0[i, j])
+        G = mpmath.eye(n)
+        G[i, i], G[j, j], G[i, j], G[j, i] = c, c, -s, s
+        ex = G.T * mpmath.matrix(a0.tolist()) * G
+        for k in range(n):
+            for l in range(n):
+                if (k, l) in ((i, j), (j, i)):
+                    continue
+                assert abs(float(ex[k, l]) - a[k, l]) <= 1e-14 * max(1.0, abs(a[k, l]))
+
+
+# ------------------------------------------------------------------ Algorithm 1
+@pytest.mark.parametrize("pivot", ["gap", "greedy"])
+def test_cache_selection_equals_brute_force(pivot):
+    """Sec. 3.2's O(n) score update gives the same pivot sequence as a full
+    scan every step (tie rule included; zeros make ties common)."""
+    rng = np.random.default_rng(7)
+    cases = [pin.config_problem("cfg1").a]
+    b = rng.standard_normal((40, 40))
+    cases.append(b + b.T)
+    c = np.diag(rng.standard_normal(24))
+    c[0, 5] = c[5, 0] = 1e-3
+    c[3, 9] = c[9, 3] = 1e-3            # equal scores, several zero entries
+    c[10, 11] = c[11, 10] = -1e-3
+    cases.append(c)
+    for a in cases:
+        n = a.shape[0]
+        r1 = oracle.jacobi(a, pivot=pivot, select="brute", tol=1e-16, log_len=100000)
+        r2 = oracle.jacobi(a, pivot=pivot, select="cache", tol=1e-16, log_len=100000)
+        assert r1["rotations"] == r2["rotations"] > 0
+        assert np.array_equal(r1["pivots"], r2["pivots"])
+        assert np.array_equal(r1["a"], r2["a"]) and np.array_equal(r1["v"], r2["v"])
+
+
+def test_first_pivot_is_brute_force_argmax():
+    """The selected pivot is the argmax of Eq. (1.1) over i<j, recomputed
+    here in mpmath for every entry."""
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal((12, 12)) * 1e-3
+    a = np.diag(np.linspace(1, 2, 12)) + b + b.T
+    r = oracle.jacobi(a, pivot="gap", log_len=1)
+    best, arg = -1, None
+    for i in range(12):
+        for j in range(i + 1, 12):
+            v = _mp_gap(a[i, i], a[j, j], a[i, j])
+            if v > best:
+                best, arg = v, (i, j)
+    assert tuple(r["pivots"][0]) == arg
+    rg = oracle.jacobi(a, pivot="greedy", log_len=1)
+    iu = np.triu_indices(12, 1)
+    k = np.argmax(np.abs(a[iu]))
+    assert tuple(rg["pivots"][0]) == (iu[0][k], iu[1][k])
+
+
+def test_cyclic_order_is_row_cyclic():
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((6, 6))
+    a = b + b.T
+    r = oracle.jacobi(a, pivot="cyclic", log_len=15, tol=1e-30, max_rot=15)
+    assert [tuple(p) for p in r["pivots"]] == [(i, j) for i in range(6) for j in range(i + 1, 6)]
+
+
+@pytest.mark.parametrize("pivot", ["gap", "greedy", "cyclic"])
+def test_known_spectrum_cfg1(pivot):
+    """Config 1 (n=32, 4 clusters x 8): eigenvalues within 1e-13 ||A||_2 of
+    the spectrum the matrix was built from; residual and orthogonality of
+    V within 1e-12; agreement with LAPACK's eigvalsh."""
+    p = pin.config_problem("cfg1")
+    r = oracle.solve(p.a, pivot=pivot, tol=1e-15)
+    assert r["status"] == 0
+    w, v = r["w"], r["v_sorted"]
+    assert np.max(np.abs(w - p.lam)) <= 1e-13 * p.norm2
+    assert np.max(np.abs(w - np.linalg.eigvalsh(p.a))) <= 1e-13 * p.norm2
+    assert np.linalg.norm(p.a @ v - v * w) / np.linalg.norm(p.a) <= 1e-12
+    assert np.linalg.norm(v.T @ v - np.eye(p.n)) <= 1e-12
+    assert r["off_final"] <= 1e-15 * r["norm_f"]
+
+
+def test_run_invariants():
+    p = pin.config_problem("cfg1")
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15)
+    a = r["a"]
+    assert abs(np.trace(a) - np.trace(a1)) <= 1e-13 * np.linalg.norm(a1)
+    assert abs(np.linalg.norm(a) - np.linalg.norm(a1)) <= 1e-13 * np.linalg.norm(a1)
+    assert np.array_equal(a, a.T)
+    # V^T A1_original V' relation: A_final = (V0^T V)^T A1 (V0^T V)
+    g = q.T @ r["v"]
+    assert np.linalg.norm(g.T @ a1 @ g - a) <= 1e-13 * np.linalg.norm(a1)
+
+
+def test_theorem1_stopping_rule():
+    """Theorem 1: when every L_ij <= eps the diagonal is within
+    2n(n-1)eps of the eigenvalues; the LIBOUND stop uses
+    eps = tol*||A||_F/(2n(n-1))."""
+    p = pin.config_problem("cfg1")
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    for tol in (1e-8, 1e-11, 1e-13):
+        r = oracle.jacobi(a1, q, pivot="gap", stop="libound", tol=tol)
+        n = p.n
+        eps = tol * r["norm_f"] / (2 * n * (n - 1))
+        a = r["a"]
+        lmax = max(oracle.gap_score(a[i, i], a[j, j], a[i, j]) for i in range(n) for j in range(i + 1, n))
+        assert lmax <= eps
+        d = np.sort(np.diag(a))
+        exact = np.linalg.eigvalsh(a)
+        assert np.max(np.abs(d - exact)) <= 2 * n * (n - 1) * eps + 1e-14
+        assert np.max(np.abs(d - p.lam)) <= 2 * n * (n - 1) * eps + 1e-14
+
+
+def test_max_rotation_budget():
+    p = pin.config_problem("cfg1")
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=10)
+    assert r["status"] == 1 and r["rotations"] == 10
+
+
+def test_offmass_and_frobenius_match_numpy():
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((17, 17))
+    a = a + a.T
+    assert abs(oracle.frobenius(a) - np.linalg.norm(a)) <= 1e-14 * np.linalg.norm(a)
+    off = np.sqrt(np.sum(a ** 2) - np.sum(np.diag(a) ** 2))
+    assert abs(oracle.offmass(a) - off) <= 1e-13 * off
+    tiny = a * 2.0 ** -700
+    assert abs(oracle.offmass(tiny) - off * 2.0 ** -700) <= 1e-13 * off * 2.0 ** -700
+
+
+# --------------------------------------------------------- Sec. 2.1 preconditioner
+def test_preconditioner_orthogonality_and_offdiag():
+    p = pin.config_problem("cfg2", n=256)
+    q0 = oracle.q0_fp32(p.a)
+    e0 = np.linalg.norm(q0.astype(np.float64).T @ q0.astype(np.float64) - np.eye(p.n))
+    assert e0 < 1e-4                              # O(u_l) in single precision
+    for reorth in ("ns", "qr"):
+        q, a1 = oracle.precondition(p.a, q0, reorth=reorth)
+        assert np.linalg.norm(q.T @ q - np.eye(p.n)) <= 1e-13
+        off = oracle.offmass(a1)
+        assert off <= 1e-4 * np.linalg.norm(p.a)      # off-diagonals O(||A|| u_l)
+        assert np.max(np.abs(np.sort(np.linalg.eigvalsh(a1)) - p.lam)) <= 1e-13 * p.norm2
+    qn, _ = oracle.precondition(p.a, q0, reorth="ns")
+    qq, _ = oracle.precondition(p.a, q0, reorth="qr")
+    assert np.max(np.abs(qn - qq)) <= 1e-6             # both stay next to Q0
+
+
+def test_exact_matmul_against_mpmath():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((6, 7))
+    y = rng.standard_normal((7, 5))
+    hi, lo = oracle.exact_matmul(x, y)
+    X, Y = mpmath.matrix(x.tolist()), mpmath.matrix(y.tolist())
+    ex = X * Y
+    for i in range(6):
+        for j in range(5):
+            assert abs(mpmath.mpf(hi[i, j]) + mpmath.mpf(lo[i, j]) - ex[i, j]) <= mpmath.mpf(2) ** -95
+
+
+def test_transform_error_is_fp64_level():
+    p = pin.config_problem("cfg2", n=128)
+    q, _ = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    a1 = oracle.transform(p.a, q)
+    ex = oracle.transform_exact(p.a, q)
+    assert np.linalg.norm(a1 - ex) / np.linalg.norm(p.a) <= 1e-14
+
+
+def test_input_generator_known_spectrum():
+    """The generator's A has the prescribed spectrum to FP64 accuracy
+    (LAPACK), and is exactly symmetric."""
+    for cfg, n in (("cfg1", None), ("cfg2", 128), ("cfg3", 128)):
+        p = pin.config_problem(cfg, n=n)
+        assert np.array_equal(p.a, p.a.T)
+        w = np.linalg.eigvalsh(p.a)
+        assert np.max(np.abs(w - p.lam)) <= 1e-14 * max(1.0, p.norm2) * p.n ** 0.5
+
+
+def test_paper_clustered_example_gap_reaches_eigenvalues_first():
+    """Sec. 4.1 (Fig. 1), reduced to n=160: with the preconditioner, the gap
+    rule reaches a given eigenvalue accuracy in fewer rotations than the
+    greedy rule for the tight cluster alpha=1."""
+    n = 160
+    lam = pin.spectrum_p1(1.0, n)
+    a = pin.exact_sym_product(pin.haar(n, np.random.default_rng(0)), lam)
+    q, a1 = oracle.precondition(a, oracle.q0_fp32(a), reorth="qr")
+    tol_e = 1e-13 * np.max(np.abs(lam))
+    rl = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, lam=lam, eig_tol=tol_e, check_every=16)
+    rg = oracle.jacobi(a1, q, pivot="greedy", tol=1e-15, lam=lam, eig_tol=tol_e, check_every=16)
+    assert 0 <= rl["first_rot_eig_ok"] < rg["first_rot_eig_ok"]
