@@ -34,7 +34,9 @@
  *   - Cyclic order: row-cyclic (0,1),(0,2),...,(0,n-1),(1,2),...; a pair
  *     whose a_ij is exactly zero is skipped (no rotation is counted).
  *   - Rotation: d = a_ii - a_jj, den = |d| + sqrt(d*d + 4*(q*q)), q = a_ij;
- *     t = sign * 2|q|/den (sign negative iff d*q < 0), which is the smaller
+ *     t = sign * 2|q|/den (sign negative iff d != 0 and d, q have opposite
+ *     signs, read from the signs, not from the product d*q which can
+ *     underflow), which is the smaller
  *     root of t^2 + 2 zeta t - 1 = 0, zeta = d/(2q), with sign(0) = +1;
  *     c = den / sqrt(den*den + 4*(q*q)) = 1/sqrt(1+t^2); s = t*c.
  *     a_ii' = fma(t,q,a_ii), a_jj' = fma(-t,q,a_jj), a_ij' = 0 exactly;
@@ -105,7 +107,7 @@ void or_rotation(double aii, double ajj, double aij, double* c, double* s, doubl
     double q2;
     double den = or_den(d, q, &q2);
     double tt = (2.0 * fabs(q)) / den;
-    if (d * q < 0.0) tt = -tt;
+    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) tt = -tt;
     double cc = den / sqrt(den * den + 4.0 * q2);
     *t = tt;
     *c = cc;

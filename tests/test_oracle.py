@@ -133,6 +133,9 @@ def test_rotation_special_cases():
     # sign of t: negative iff (a_ii - a_jj) * a_ij < 0
     assert oracle.rotation(2.0, 1.0, 0.1)[2] > 0 and oracle.rotation(1.0, 2.0, 0.1)[2] < 0
     assert oracle.rotation(2.0, 1.0, -0.1)[2] < 0 and oracle.rotation(1.0, 2.0, -0.1)[2] > 0
+    # the product (a_ii - a_jj) * a_ij underflows here; the sign must survive
+    assert oracle.rotation(1e-150, 0.0, -1e-300)[2] < 0
+    assert oracle.rotation(0.0, 1e-150, -1e-300)[2] > 0
 
 
 def test_single_rotation_invariants():
