@@ -1,0 +1,223 @@
+/*
+ * pjac -- preconditioned Jacobi eigensolver with perturbation-inspired
+ * (spectral-gap-weighted) pivoting, for NVIDIA B300 (sm_103a).
+ *
+ * Method: Shao & Nakatsukasa, "Accelerating preconditioned Jacobi methods
+ * via perturbation-inspired pivoting".  A symmetric A is first brought close
+ * to diagonal by a mixed-precision preconditioner (Sec. 2.1): an FP32
+ * spectral decomposition Q0 ~ eig(fl32(A)), reorthogonalised to an
+ * FP64-orthogonal Q, then A1 = Q^T A Q.  Jacobi's method (Algorithm 1,
+ * Sec. 2) then annihilates the off-diagonal entries of A1 with one of three
+ * pivot rules: the gap-weighted rule of Eq. (1.1),
+ *     L_ij = 2|a_ij|^2 / (|a_ii-a_jj| + sqrt(|a_ii-a_jj|^2 + 4|a_ij|^2)),
+ * Jacobi's classical greedy argmax|a_ij|, or cyclic sweeps (Sec. 1).  The
+ * eigenvalues are the final diagonal; the eigenvectors are V = Q * prod G.
+ *
+ * Conventions for every call:
+ *   - Matrices are DEVICE pointers to FP64 column-major storage with a
+ *     leading dimension (>= n).  A symmetric input is read in full; the
+ *     caller must pass an exactly symmetric matrix (A[i,j] == A[j,i]).
+ *   - The caller owns every buffer it passes.  The handle owns its
+ *     workspace (device memory sized on first use, grown on demand).
+ *   - Calls are asynchronous on the given stream unless stated otherwise.
+ *   - Every call returns a pjac_status; PJAC_OK is 0.  On failure a message
+ *     is available from pjac_last_error() (per thread).
+ *   - Sizes: 1 <= n <= PJAC_MAX_N.  n == 1 is trivial (W = A, V = 1).
+ *   - Index pairs (i,j) are 0-based with i < j.
+ */
+#ifndef PJAC_H
+#define PJAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PJAC_MAX_N 16384
+
+/* Status codes. */
+typedef enum {
+    PJAC_OK = 0,
+    PJAC_PENDING = 1,      /* serving: request not finished yet */
+    PJAC_EINVAL = -1,      /* bad argument (n, leading dimension, pointer, NaN/Inf input) */
+    PJAC_ENOMEM = -2,      /* device allocation failed */
+    PJAC_EAGAIN = -3,      /* serving: queue full, retry later */
+    PJAC_ENOCONV = -4,     /* rotation budget reached; W, V are valid but not converged */
+    PJAC_ETIMEOUT = -5,    /* a device-side time budget ran out; results partial */
+    PJAC_ECUDA = -6,       /* a CUDA runtime call failed */
+    PJAC_ENOTIMPL = -7     /* option not available */
+} pjac_status;
+
+/* Pivot rules (Sec. 1, Eq. (1.1)). */
+typedef enum {
+    PJAC_PIVOT_GAP = 0,     /* argmax L_ij of Eq. (1.1) */
+    PJAC_PIVOT_GREEDY = 1,  /* argmax |a_ij| (Jacobi 1846) */
+    PJAC_PIVOT_CYCLIC = 2   /* row-cyclic sweeps (0,1),(0,2),...,(n-2,n-1) */
+} pjac_pivot;
+
+/* Stopping rules. */
+typedef enum {
+    /* off(A1) = sqrt(sum_{i!=j} a_ij^2) <= tol * ||A1||_F, tested every n
+     * rotations (gap, greedy) or before every sweep (cyclic). */
+    PJAC_STOP_OFFDIAG = 0,
+    /* Theorem 1 (Sec. 3.1): stop when max L_ij <= tol*||A1||_F/(2n(n-1)),
+     * which guarantees |lambda_k - a_kk| <= tol*||A1||_F.  Eigenvalues only:
+     * V is then NOT accurate to working precision. Gap rule only. */
+    PJAC_STOP_LIBOUND = 1
+} pjac_stop;
+
+/* How A1 = Q^T A Q and the Newton--Schulz products are formed. */
+typedef enum {
+    PJAC_TRANSFORM_SPLIT_BF16 = 0, /* tensor cores: BF16 slices, FP32 accumulate, FP64 recombine */
+    PJAC_TRANSFORM_FP64 = 1        /* plain FP64 products on the CUDA cores */
+} pjac_transform;
+
+typedef struct {
+    pjac_stop stop;          /* default PJAC_STOP_OFFDIAG */
+    double tol;              /* default 1e-15 */
+    int64_t max_rotations;   /* 0: 50 * n(n-1)/2 */
+    int64_t check_every;     /* 0: n (off-mass test period, gap/greedy) */
+    pjac_transform transform;/* default PJAC_TRANSFORM_SPLIT_BF16 */
+    int ns_steps;            /* Newton--Schulz steps, 0: 3 */
+    int cluster_size;        /* CTAs cooperating on one single problem; 0: automatic */
+    double time_budget_s;    /* device-side time budget per solve, 0: 600 s */
+} pjac_opts;
+
+/* Per-solve report. */
+typedef struct {
+    int64_t rotations;       /* rotations applied */
+    double sweeps;           /* rotations / (n(n-1)/2), or sweeps for cyclic */
+    double off_rel;          /* off(A_final) / ||A1||_F */
+    double max_score;        /* last selected pivot score (L_ij or |a_ij|) */
+    int32_t status;          /* pjac_status of this solve */
+    int32_t n;
+    float ms_precond;        /* FP32 diagonalisation + reorthogonalisation */
+    float ms_transform;      /* Q^T A Q */
+    float ms_jacobi;         /* Jacobi iteration + readout */
+} pjac_info;
+
+typedef struct pjac_handle pjac_handle;
+
+/* Default options (stop OFFDIAG, tol 1e-15, split-BF16 transform, 3 NS steps). */
+void pjac_default_opts(pjac_opts* o);
+
+/* Create a handle bound to the current CUDA device.  o may be NULL.
+ * Errors: PJAC_EINVAL (h NULL), PJAC_ECUDA. */
+int pjac_create(pjac_handle** h, const pjac_opts* o);
+/* Release the handle and its workspace (synchronises the device). */
+int pjac_destroy(pjac_handle* h);
+/* Replace the handle's options. */
+int pjac_set_opts(pjac_handle* h, const pjac_opts* o);
+
+/*
+ * Mixed-precision preconditioner (Sec. 2.1).
+ *   A   [in]  n x n symmetric, lda >= n.  Not modified.
+ *   Q0  [in]  optional n x n FP32 approximate eigenvectors (column-major,
+ *             leading dimension n).  NULL: computed on the device by an FP32
+ *             parallel-order Jacobi diagonalisation of fl32(A).
+ *   Q   [out] n x n FP64 orthogonal to working precision (Newton--Schulz
+ *             X <- X(3I - X^T X)/2 from X = Q0), ldq >= n.
+ *   A1  [out] Q^T A Q symmetrised ((A1 + A1^T)/2), lda1 >= n.
+ * Errors: PJAC_EINVAL, PJAC_ENOMEM, PJAC_ECUDA.
+ */
+int pjac_precondition(pjac_handle* h, const double* A, int n, int lda, const float* Q0,
+                      double* Q, int ldq, double* A1, int lda1, void* stream);
+
+/*
+ * Full solve: preconditioner, then Algorithm 1 on A1 with V0 = Q, then the
+ * readout (W ascending, V's columns in the same order).
+ *   A   [in]  n x n symmetric, not modified.
+ *   W   [out] n eigenvalues ascending.
+ *   V   [out] n x n eigenvectors (column k for W[k]), ldv >= n.
+ *   info [out, host, nullable] filled after the solve; this call
+ *        synchronises the stream when info != NULL.
+ * Returns PJAC_OK, PJAC_ENOCONV, PJAC_ETIMEOUT or an error.
+ */
+int pjac_solve(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol,
+               double* W, double* V, int ldv, pjac_info* info, void* stream);
+
+/*
+ * Algorithm 1 on an already preconditioned A1 (overwritten with the final,
+ * nearly diagonal matrix).  V0 [in] n x n (NULL: identity), ldv0 >= n;
+ * V [out] the accumulated V0 * prod G with columns sorted like W.
+ * Same returns as pjac_solve.
+ */
+int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int lda1, const double* V0,
+                              int ldv0, pjac_pivot pivot, double tol, double* W, double* V,
+                              int ldv, pjac_info* info, void* stream);
+
+/*
+ * Batched form: nb independent problems of order n[p] (2 <= n[p] <= 1024)
+ * packed in one device buffer.  Host arrays n, a_off, w_off, v_off give each
+ * problem's order and its offsets (in doubles) into A, W and V; problem p is
+ * column-major with leading dimension n[p].  A is not modified.  Each problem
+ * is preconditioned and solved like pjac_solve.  infos [out, DEVICE] nb
+ * records, written by the device (graph-capturable: no host sync).
+ * Returns PJAC_OK once the work is enqueued; per-problem status is in infos.
+ */
+int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_off,
+                       const double* A, const int64_t* w_off, double* W, const int64_t* v_off,
+                       double* V, pjac_pivot pivot, double tol, pjac_info* infos, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: continuous batching of eigenproblems of mixed sizes.  Requests
+ * are admitted while their device footprint fits the memory budget and a
+ * slot is free; admitted requests run concurrently on the device; finished
+ * slots are recycled immediately for waiting requests.
+ * ------------------------------------------------------------------- */
+typedef struct pjac_server pjac_server;
+
+typedef struct {
+    int max_slots;            /* concurrently admitted requests, 0: 64 */
+    int max_queue;            /* waiting (not yet admitted) requests, 0: 1 << 16 */
+    size_t hbm_budget_bytes;  /* device bytes for admitted requests, 0: 8 GiB */
+    pjac_opts solver;         /* options of every solve */
+} pjac_serve_opts;
+
+void pjac_serve_default_opts(pjac_serve_opts* o);
+int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o);
+/* Waits for in-flight work, then frees everything. */
+int pjac_serve_destroy(pjac_server* s);
+
+/*
+ * Submit one request (non-blocking).  A [in, HOST] n x n symmetric,
+ * column-major, lda >= n; copied before the call returns.  W [out, HOST]
+ * n doubles, V [out, HOST, nullable] n x n with ldv >= n: written when the
+ * request completes and must stay valid until pjac_serve_poll returns a
+ * terminal status for the ticket.  Returns PJAC_EAGAIN when the waiting
+ * queue is full.
+ */
+int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda, pjac_pivot pivot,
+                      double tol, double* W, double* V, int ldv, uint64_t* ticket);
+
+/* Progress the server and report on one ticket: PJAC_PENDING while queued
+ * or running, else the request's final status (info filled, nullable). A
+ * ticket can be polled to completion once. */
+int pjac_serve_poll(pjac_server* s, uint64_t ticket, pjac_info* info);
+
+/* Progress the server without asking about a ticket; returns the number of
+ * requests still queued or running. */
+int pjac_serve_progress(pjac_server* s);
+
+/* Latency statistics (milliseconds from submit to completion) over the
+ * completed requests so far. */
+typedef struct {
+    int64_t completed;
+    double p50_ms, p99_ms, max_ms, mean_ms;
+    double solves_per_s;      /* completed / (last completion - first submission) */
+    int64_t peak_inflight;
+    size_t peak_hbm_bytes;
+} pjac_serve_stats;
+int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
+
+/* Human-readable text for a status code (static storage). */
+const char* pjac_status_string(int status);
+/* Last error message of the calling thread (static per-thread storage). */
+const char* pjac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PJAC_H */

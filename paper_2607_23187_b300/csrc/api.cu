@@ -1,0 +1,454 @@
+// C ABI of libpjac: handle, argument checks, and the single-problem pipeline
+// (Sec. 2.1 preconditioner, then Algorithm 1, then the readout).
+#include <cuda_runtime.h>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+#include "internal.h"
+
+using namespace pjac;
+
+namespace pjac {
+static thread_local char g_err[512] = "";
+
+int set_err(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_err(cudaError_t e, const char* what) {
+    return set_err(PJAC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+}  // namespace pjac
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return pjac::cuda_err(e_, #call);    \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need) {
+        if (need <= bytes) return PJAC_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(PJAC_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
+        }
+        bytes = need;
+        return PJAC_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+struct pjac_handle {
+    pjac_opts opts;
+    int device;
+    DevBuf ws;          // main workspace
+    DevBuf tcws;        // tensor-core product workspace
+    cudaEvent_t ev[4];
+    std::mutex mu;
+};
+
+extern "C" void pjac_default_opts(pjac_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->stop = PJAC_STOP_OFFDIAG;
+    o->tol = 1e-15;
+    o->max_rotations = 0;
+    o->check_every = 0;
+    o->transform = PJAC_TRANSFORM_FP64;
+    o->ns_steps = 3;
+    o->cluster_size = 0;
+    o->time_budget_s = 600.0;
+}
+
+static int validate_opts(const pjac_opts* o) {
+    if (o->stop != PJAC_STOP_OFFDIAG && o->stop != PJAC_STOP_LIBOUND)
+        return set_err(PJAC_EINVAL, "opts.stop must be PJAC_STOP_OFFDIAG or PJAC_STOP_LIBOUND");
+    if (!(o->tol >= 0.0) || o->tol != o->tol) return set_err(PJAC_EINVAL, "opts.tol must be >= 0");
+    if (o->max_rotations < 0 || o->check_every < 0) return set_err(PJAC_EINVAL, "negative budget");
+    if (o->transform != PJAC_TRANSFORM_SPLIT_BF16 && o->transform != PJAC_TRANSFORM_FP64)
+        return set_err(PJAC_EINVAL, "opts.transform invalid");
+    if (o->ns_steps < 0 || o->ns_steps > 10) return set_err(PJAC_EINVAL, "opts.ns_steps must be in [0,10]");
+    if (o->cluster_size < 0 || o->cluster_size > 16 || (o->cluster_size & (o->cluster_size - 1)))
+        return set_err(PJAC_EINVAL, "opts.cluster_size must be 0 or a power of two <= 16");
+    return PJAC_OK;
+}
+
+extern "C" int pjac_create(pjac_handle** h, const pjac_opts* o) {
+    if (!h) return set_err(PJAC_EINVAL, "h is NULL");
+    *h = nullptr;
+    pjac_opts d;
+    pjac_default_opts(&d);
+    if (o) d = *o;
+    int r = validate_opts(&d);
+    if (r) return r;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    pjac_handle* p = new pjac_handle();
+    p->opts = d;
+    p->device = dev;
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t e = cudaEventCreate(&p->ev[k]);
+        if (e != cudaSuccess) {
+            delete p;
+            return cuda_err(e, "cudaEventCreate");
+        }
+    }
+    *h = p;
+    return PJAC_OK;
+}
+
+void pjac_batched_release(const void* h);
+
+namespace pjac {
+int handle_opts(const pjac_handle* h, pjac_opts* o) {
+    *o = h->opts;
+    return PJAC_OK;
+}
+}  // namespace pjac
+
+extern "C" int pjac_destroy(pjac_handle* h) {
+    if (!h) return PJAC_OK;
+    cudaDeviceSynchronize();
+    pjac_batched_release(h);
+    h->ws.release();
+    h->tcws.release();
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(h->ev[k]);
+    delete h;
+    return PJAC_OK;
+}
+
+extern "C" int pjac_set_opts(pjac_handle* h, const pjac_opts* o) {
+    if (!h || !o) return set_err(PJAC_EINVAL, "NULL argument");
+    int r = validate_opts(o);
+    if (r) return r;
+    h->opts = *o;
+    return PJAC_OK;
+}
+
+static int check_dims(int n, int ld, const char* name) {
+    if (n < 1 || n > PJAC_MAX_N) return set_err(PJAC_EINVAL, "n = %d out of range [1, %d]", n, PJAC_MAX_N);
+    if (ld < n) return set_err(PJAC_EINVAL, "%s = %d < n = %d", name, ld, n);
+    return PJAC_OK;
+}
+
+static int check_input(pjac_handle* h, const double* A, long long lda, int n, cudaStream_t st, int* flag) {
+    CK(check_finite(A, lda, n, flag, st));
+    int hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    (void)h;
+    if (hflag & 1) return set_err(PJAC_EINVAL, "input contains NaN or Inf");
+    if (hflag & 2) return set_err(PJAC_EINVAL, "input is not exactly symmetric");
+    return PJAC_OK;
+}
+
+// Workspace layout of one single-problem solve (doubles unless noted).
+struct SolveWs {
+    double* A1;    // n x n
+    double* Vw;    // n x n
+    double* T;     // n x n
+    double* Y;     // n x n
+    double* Wd;    // n
+    float* Q0;     // n x n
+    float* d32;    // diag_fp32 workspace
+    int* rank;     // n
+    int* flag;     // 1
+    DevInfo* info; // 1
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int layout_ws(pjac_handle* h, int n, SolveWs* w) {
+    size_t nn = (size_t)n * n;
+    size_t sz[10] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
+                     diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo)};
+    size_t tot = 0;
+    for (size_t s : sz) tot += align256(s);
+    int r = h->ws.ensure(tot);
+    if (r) return r;
+    char* p = static_cast<char*>(h->ws.p);
+    void* ptrs[10];
+    for (int k = 0; k < 10; ++k) {
+        ptrs[k] = p;
+        p += align256(sz[k]);
+    }
+    w->A1 = (double*)ptrs[0];
+    w->Vw = (double*)ptrs[1];
+    w->T = (double*)ptrs[2];
+    w->Y = (double*)ptrs[3];
+    w->Wd = (double*)ptrs[4];
+    w->Q0 = (float*)ptrs[5];
+    w->d32 = (float*)ptrs[6];
+    w->rank = (int*)ptrs[7];
+    w->flag = (int*)ptrs[8];
+    w->info = (DevInfo*)ptrs[9];
+    return PJAC_OK;
+}
+
+// C = op(A) op(B) with the product chosen by the options.
+static int product(pjac_handle* h, bool ta, bool tb, int n, double alpha, const double* A, long long lda,
+                   const double* B, long long ldb, double beta, double* C, long long ldc, cudaStream_t st) {
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16) {
+        size_t need = gemm_split_bf16_ws(n, n, n);
+        if (need > 0) {
+            int r = h->tcws.ensure(need);
+            if (r) return r;
+            cudaError_t e = gemm_split_bf16(ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, h->tcws.p,
+                                            h->tcws.bytes, st);
+            if (e == cudaSuccess) return PJAC_OK;
+            if (e != cudaErrorNotSupported) return cuda_err(e, "gemm_split_bf16");
+            cudaGetLastError();
+            return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available for this shape");
+        }
+        return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available");
+    }
+    CK(gemm_f64(ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, st));
+    return PJAC_OK;
+}
+
+// Sec. 2.1 into workspace: Q (ld n) and A1 (ld n).  Records ev[0..2].
+static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda, const float* Q0,
+                           double* Q, long long ldq, double* A1, long long lda1, SolveWs& w, cudaStream_t st) {
+    CK(cudaEventRecord(h->ev[0], st));
+    const float* q0 = Q0;
+    long long ldq0 = n;
+    if (!q0) {
+        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 15, st));
+        q0 = w.Q0;
+    }
+    // X = fl64(Q0);  X <- X (3I - X^T X) / 2
+    CK(copy_f32_to_f64(q0, ldq0, Q, ldq, n, st));
+    int steps = h->opts.ns_steps;
+    for (int it = 0; it < steps; ++it) {
+        int r = product(h, true, false, n, 1.0, Q, ldq, Q, ldq, 0.0, w.Y, n, st);
+        if (r) return r;
+        CK(three_i_minus(w.Y, n, n, st));
+        r = product(h, false, false, n, 0.5, Q, ldq, w.Y, n, 0.0, w.T, n, st);
+        if (r) return r;
+        CK(copy_f64(w.T, n, Q, ldq, n, n, st));
+    }
+    CK(cudaEventRecord(h->ev[1], st));
+    // A1 = Q^T (A Q), symmetrised
+    int r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);
+    if (r) return r;
+    r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
+    if (r) return r;
+    CK(symmetrize(A1, lda1, n, st));
+    CK(cudaEventRecord(h->ev[2], st));
+    return PJAC_OK;
+}
+
+extern "C" int pjac_precondition(pjac_handle* h, const double* A, int n, int lda, const float* Q0,
+                                 double* Q, int ldq, double* A1, int lda1, void* stream) {
+    if (!h || !A || !Q || !A1) return set_err(PJAC_EINVAL, "NULL argument");
+    int r = check_dims(n, lda, "lda");
+    if (!r) r = check_dims(n, ldq, "ldq");
+    if (!r) r = check_dims(n, lda1, "lda1");
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveWs w;
+    r = layout_ws(h, n, &w);
+    if (r) return r;
+    r = check_input(h, A, lda, n, st, w.flag);
+    if (r) return r;
+    return precondition_ws(h, A, n, lda, Q0, Q, ldq, A1, lda1, w, st);
+}
+
+static long long budget_cycles(const pjac_opts& o) {
+    double s = o.time_budget_s > 0 ? o.time_budget_s : 600.0;
+    return (long long)(s * 2.2e9);   // cycles at the maximum SM clock (upper bound on time)
+}
+
+static int run_jacobi(pjac_handle* h, double* A1, long long lda1, int n, double* Vw, long long ldvw,
+                      pjac_pivot pivot, double tol, double* Wd, DevInfo* dinfo, cudaStream_t st) {
+    JacArgs a;
+    a.A = A1;
+    a.lda = lda1;
+    a.V = Vw;
+    a.ldv = ldvw;
+    a.Wd = Wd;
+    a.n = n;
+    a.pivot = (int)pivot;
+    a.stop = (int)h->opts.stop;
+    a.tol = tol;
+    long long pairs = (long long)n * (n - 1) / 2;
+    a.max_rot = h->opts.max_rotations > 0 ? h->opts.max_rotations : 50 * pairs;
+    a.check_every = h->opts.check_every > 0 ? h->opts.check_every : n;
+    a.budget_cycles = budget_cycles(h->opts);
+    a.info = dinfo;
+    int P = h->opts.cluster_size > 0 ? h->opts.cluster_size : jacobi_auto_cluster(n);
+    while (P > 1 && (n + P - 1) / P < 8) P >>= 1;
+    if ((n + P - 1) / P > 1024) return set_err(PJAC_EINVAL, "n = %d needs a larger cluster", n);
+    CK(launch_jacobi(a, P, st));
+    return PJAC_OK;
+}
+
+static int finish_info(pjac_handle* h, DevInfo* dinfo, pjac_info* info, cudaStream_t st, bool timed) {
+    DevInfo d;
+    CK(cudaMemcpyAsync(&d, dinfo, sizeof(d), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (info) {
+        info->rotations = d.rotations;
+        double pairs = 0.5 * (double)d.n * (double)(d.n - 1);
+        info->sweeps = d.sweeps > 0 ? (double)d.sweeps : (pairs > 0 ? d.rotations / pairs : 0.0);
+        info->off_rel = d.normf > 0 ? d.off / d.normf : 0.0;
+        info->max_score = d.max_score;
+        info->status = d.status;
+        info->n = d.n;
+        info->ms_precond = info->ms_transform = info->ms_jacobi = 0.f;
+        if (timed) {
+            cudaEventElapsedTime(&info->ms_precond, h->ev[0], h->ev[1]);
+            cudaEventElapsedTime(&info->ms_transform, h->ev[1], h->ev[2]);
+            cudaEventElapsedTime(&info->ms_jacobi, h->ev[2], h->ev[3]);
+        }
+    }
+    return d.status == PJAC_OK ? PJAC_OK
+                               : set_err(d.status, "solve ended with status %d after %lld rotations", d.status,
+                                         (long long)d.rotations);
+}
+
+static int trivial_n1(const double* A, double* W, double* V, cudaStream_t st, pjac_info* info) {
+    CK(cudaMemcpyAsync(W, A, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (V) {
+        double one = 1.0;
+        CK(cudaMemcpyAsync(V, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->n = 1;
+    }
+    return PJAC_OK;
+}
+
+static int solve_checks(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol,
+                        const double* W, const double* V, int ldv) {
+    if (!h || !A || !W) return set_err(PJAC_EINVAL, "NULL argument");
+    int r = check_dims(n, lda, "lda");
+    if (!r && V) r = check_dims(n, ldv, "ldv");
+    if (r) return r;
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    if (h->opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
+        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+    return PJAC_OK;
+}
+
+// Preconditioner, Jacobi, readout: all enqueued on st, no host round trip.
+static int solve_pipeline(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol,
+                          double* W, double* V, int ldv, SolveWs& w, cudaStream_t st) {
+    int r = precondition_ws(h, A, n, lda, nullptr, w.Vw, n, w.A1, n, w, st);
+    if (r) return r;
+    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    if (r) return r;
+    CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
+    CK(cudaEventRecord(h->ev[3], st));
+    return PJAC_OK;
+}
+
+extern "C" int pjac_solve(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol,
+                          double* W, double* V, int ldv, pjac_info* info, void* stream) {
+    int r = solve_checks(h, A, n, lda, pivot, tol, W, V, ldv);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 1) return trivial_n1(A, W, V, st, info);
+    std::lock_guard<std::mutex> lk(h->mu);
+    SolveWs w;
+    r = layout_ws(h, n, &w);
+    if (r) return r;
+    r = check_input(h, A, lda, n, st, w.flag);
+    if (r) return r;
+    r = solve_pipeline(h, A, n, lda, pivot, tol, W, V, ldv, w, st);
+    if (r) return r;
+    return finish_info(h, w.info, info, st, true);
+}
+
+namespace pjac {
+// Asynchronous single-problem solve for the serving lanes: the input was
+// validated on the host; the report is written to device memory (dinfo)
+// by the device.  Nothing here waits for the device.
+int solve_async_dev(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol, double* W,
+                    double* V, int ldv, pjac_info* dinfo, cudaStream_t st) {
+    int r = solve_checks(h, A, n, lda, pivot, tol, W, V, ldv);
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(h->mu);
+    SolveWs w;
+    r = layout_ws(h, n, &w);
+    if (r) return r;
+    r = solve_pipeline(h, A, n, lda, pivot, tol, W, V, ldv, w, st);
+    if (r) return r;
+    CK(launch_info_single(w.info, dinfo, st));
+    return PJAC_OK;
+}
+}  // namespace pjac
+
+extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int lda1, const double* V0,
+                                         int ldv0, pjac_pivot pivot, double tol, double* W, double* V,
+                                         int ldv, pjac_info* info, void* stream) {
+    if (!h || !A1 || !W) return set_err(PJAC_EINVAL, "NULL argument");
+    int r = check_dims(n, lda1, "lda1");
+    if (!r && V0) r = check_dims(n, ldv0, "ldv0");
+    if (!r && V) r = check_dims(n, ldv, "ldv");
+    if (r) return r;
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    if (h->opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
+        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 1) return trivial_n1(A1, W, V, st, info);
+    std::lock_guard<std::mutex> lk(h->mu);
+    SolveWs w;
+    r = layout_ws(h, n, &w);
+    if (r) return r;
+    r = check_input(h, A1, lda1, n, st, w.flag);
+    if (r) return r;
+    CK(cudaEventRecord(h->ev[0], st));
+    CK(cudaEventRecord(h->ev[1], st));
+    if (V0) {
+        CK(copy_f64(V0, ldv0, w.Vw, n, n, n, st));
+    } else {
+        CK(set_identity(w.Vw, n, n, st));
+    }
+    CK(cudaEventRecord(h->ev[2], st));
+    r = run_jacobi(h, A1, lda1, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    if (r) return r;
+    CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
+    CK(cudaEventRecord(h->ev[3], st));
+    return finish_info(h, w.info, info, st, true);
+}
+
+extern "C" const char* pjac_status_string(int s) {
+    switch (s) {
+        case PJAC_OK: return "PJAC_OK";
+        case PJAC_PENDING: return "PJAC_PENDING";
+        case PJAC_EINVAL: return "PJAC_EINVAL: invalid argument";
+        case PJAC_ENOMEM: return "PJAC_ENOMEM: device allocation failed";
+        case PJAC_EAGAIN: return "PJAC_EAGAIN: queue full";
+        case PJAC_ENOCONV: return "PJAC_ENOCONV: rotation budget reached";
+        case PJAC_ETIMEOUT: return "PJAC_ETIMEOUT: device time budget ran out";
+        case PJAC_ECUDA: return "PJAC_ECUDA: CUDA runtime error";
+        case PJAC_ENOTIMPL: return "PJAC_ENOTIMPL: not available";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* pjac_last_error(void) { return pjac::g_err; }

@@ -1,0 +1,370 @@
+// Batched form: thousands of independent eigenproblems of mixed orders in
+// one stream of device work, without host synchronisation (so a call can be
+// captured in a CUDA graph).  Every problem follows the single-problem
+// pipeline: FP32 diagonalisation of fl32(A) (Sec. 2.1, u_l = single),
+// Newton--Schulz reorthogonalisation, A1 = Q^T A Q, Algorithm 1, readout.
+//
+// Each stage is one launch of persistent CTAs that take problems from a
+// device work queue, largest order first.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include "internal.h"
+
+namespace pjac {
+
+int set_err(int code, const char* fmt, ...);
+int cuda_err(cudaError_t e, const char* what);
+
+constexpr int BT = 256;          // threads per CTA of the batched stages
+constexpr int SMEM_N32 = 128;    // FP32 diagonaliser state in shared memory up to this order
+
+__device__ __forceinline__ int take_problem(int* counter, int* sh_next) {
+    if (threadIdx.x == 0) *sh_next = atomicAdd(counter, 1);
+    __syncthreads();
+    int t = *sh_next;
+    __syncthreads();
+    return t;
+}
+
+__device__ __forceinline__ void rot32b(float app, float aqq, float apq, float& c, float& s) {
+    if (apq == 0.0f) { c = 1.0f; s = 0.0f; return; }
+    float d = app - aqq;
+    float den = fabsf(d) + sqrtf(d * d + 4.0f * apq * apq);
+    float t = 2.0f * fabsf(apq) / den;
+    if (d != 0.0f && ((d < 0.0f) != (apq < 0.0f))) t = -t;
+    c = rsqrtf(1.0f + t * t);
+    s = t * c;
+}
+
+// Round-robin tournament (circle method) on N players (N even): in round r
+// pair 0 is (N-1, r) and pair k >= 1 is ((r+k) mod (N-1), (r-k) mod (N-1)).
+__device__ __forceinline__ void rr_pair(int r, int k, int N, int& p, int& q) {
+    if (k == 0) { p = N - 1; q = r; }
+    else {
+        p = (r + k) % (N - 1);
+        q = (r - k + (N - 1)) % (N - 1);
+    }
+    if (p > q) { int t = p; p = q; q = t; }
+}
+
+// Stage 1: FP32 parallel-order Jacobi on fl32(A) per problem.
+__global__ void __launch_bounds__(BT) b_diag32_kernel(const BatchDesc* desc, int nb, const int* order,
+                                                      int* counter, int max_sweeps) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ int next;
+    __shared__ float cs[512][2];
+    __shared__ short pp[512][2];
+    __shared__ double red[BT / 32][2];
+    __shared__ int stop;
+    for (;;) {
+        int t = take_problem(counter, &next);
+        if (t >= nb) break;
+        BatchDesc d = desc[order[t]];
+        const int n = d.n;
+        const int N = n + (n & 1);
+        const int npairs = N / 2;
+        float* A = (n <= SMEM_N32) ? reinterpret_cast<float*>(dyn) : d.A32;
+        float* Q = (n <= SMEM_N32) ? reinterpret_cast<float*>(dyn) + n * n : d.Q32;
+        for (int e = threadIdx.x; e < n * n; e += BT) {
+            int r = e % n, c = e / n;
+            A[e] = (float)d.Ain[e];
+            Q[e] = (r == c) ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+        double prev = -1.0;
+        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+            for (int r = 0; r < N - 1; ++r) {
+                for (int k = threadIdx.x; k < npairs; k += BT) {
+                    int p, q;
+                    rr_pair(r, k, N, p, q);
+                    float c = 1.0f, s = 0.0f;
+                    if (q < n) rot32b(A[p + p * n], A[q + q * n], A[p + q * n], c, s);
+                    cs[k][0] = c; cs[k][1] = s;
+                    pp[k][0] = (short)p; pp[k][1] = (short)q;
+                }
+                __syncthreads();
+                // A <- G^T A G on 2x2 blocks (pair a rows, pair b cols), in place
+                for (int e = threadIdx.x; e < npairs * npairs; e += BT) {
+                    int a = e % npairs, b = e / npairs;
+                    int pa = pp[a][0], qa = pp[a][1], pb = pp[b][0], qb = pp[b][1];
+                    if (qa >= n || qb >= n) continue;   // dummy player of odd n
+                    float ca = cs[a][0], sa = cs[a][1], cb = cs[b][0], sb = cs[b][1];
+                    float x00 = A[pa + pb * n], x10 = A[qa + pb * n];
+                    float x01 = A[pa + qb * n], x11 = A[qa + qb * n];
+                    float y00 = ca * x00 + sa * x10, y10 = -sa * x00 + ca * x10;
+                    float y01 = ca * x01 + sa * x11, y11 = -sa * x01 + ca * x11;
+                    float z00 = y00 * cb + y01 * sb, z01 = -y00 * sb + y01 * cb;
+                    float z10 = y10 * cb + y11 * sb, z11 = -y10 * sb + y11 * cb;
+                    if (a == b && sa != 0.0f) { z01 = 0.0f; z10 = 0.0f; }
+                    A[pa + pb * n] = z00; A[qa + pb * n] = z10;
+                    A[pa + qb * n] = z01; A[qa + qb * n] = z11;
+                }
+                // Q <- Q G on column pairs
+                for (int e = threadIdx.x; e < n * npairs; e += BT) {
+                    int row = e % n, k = e / n;
+                    int p = pp[k][0], q = pp[k][1];
+                    if (q >= n) continue;
+                    float c = cs[k][0], s = cs[k][1];
+                    float q0 = Q[row + p * n], q1 = Q[row + q * n];
+                    Q[row + p * n] = q0 * c + q1 * s;
+                    Q[row + q * n] = -q0 * s + q1 * c;
+                }
+                __syncthreads();
+            }
+            // convergence: off^2 vs ||A||^2 (FP64 accumulation)
+            double off = 0.0, all = 0.0;
+            for (int e = threadIdx.x; e < n * n; e += BT) {
+                double v = (double)A[e];
+                all += v * v;
+                if (e % n != e / n) off += v * v;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                off += __shfl_xor_sync(0xffffffffu, off, o);
+                all += __shfl_xor_sync(0xffffffffu, all, o);
+            }
+            if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = off; red[threadIdx.x >> 5][1] = all; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double o2 = 0, a2 = 0;
+                for (int w = 0; w < BT / 32; ++w) { o2 += red[w][0]; a2 += red[w][1]; }
+                int st = 0;
+                if (a2 == 0.0 || o2 <= 1e-13 * a2) st = 1;
+                else if (prev >= 0.0 && sweep >= 3 && o2 > 0.25 * prev) st = 1;
+                prev = o2;
+                stop = st;
+            }
+            __syncthreads();
+            if (stop) break;
+        }
+        for (int e = threadIdx.x; e < n * n; e += BT) d.Q32[e] = Q[e];
+        __syncthreads();
+    }
+}
+
+// C = alpha * op(X) * op(Y), n x n, all leading dimensions n, inside one CTA.
+__device__ void cta_gemm(bool tx, bool ty, int n, double alpha, const double* X, const double* Y,
+                         double* C, double (*Xs)[65], double (*Ys)[65]) {
+    const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+    for (int m0 = 0; m0 < n; m0 += 64)
+        for (int n0 = 0; n0 < n; n0 += 64) {
+            double acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+            for (int k0 = 0; k0 < n; k0 += 16) {
+                for (int e = threadIdx.x; e < 64 * 16; e += BT) {
+                    int mm = e % 64, kk = e / 64;
+                    int gi = m0 + mm, gk = k0 + kk;
+                    double v = 0.0;
+                    if (gi < n && gk < n) v = tx ? X[gk + gi * n] : X[gi + gk * n];
+                    Xs[kk][mm] = v;
+                    int nn = e % 64;
+                    int gj = n0 + nn;
+                    double w = 0.0;
+                    if (gj < n && gk < n) w = ty ? Y[gj + gk * n] : Y[gk + gj * n];
+                    Ys[kk][nn] = w;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    double av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = Xs[kk][ti + 16 * a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = Ys[kk][tj + 16 * b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = __fma_rn(av[a], bv[b], acc[a][b]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    int gi = m0 + ti + 16 * a, gj = n0 + tj + 16 * b;
+                    if (gi < n && gj < n) C[gi + gj * n] = alpha * acc[a][b];
+                }
+        }
+    __syncthreads();
+}
+
+// Stage 2: Newton--Schulz X <- X(3I - X^T X)/2 from X = fl64(Q0), then
+// A1 = X^T A X symmetrised.  V holds X (it becomes V0 = Q of the iteration).
+__global__ void __launch_bounds__(BT) b_precond_kernel(const BatchDesc* desc, int nb, const int* order,
+                                                       int* counter, int ns_steps) {
+    __shared__ double Xs[16][65], Ys[16][65];
+    __shared__ int next;
+    for (;;) {
+        int t = take_problem(counter, &next);
+        if (t >= nb) break;
+        BatchDesc d = desc[order[t]];
+        const int n = d.n;
+        for (int e = threadIdx.x; e < n * n; e += BT) d.V[e] = (double)d.Q32[e];
+        __syncthreads();
+        for (int it = 0; it < ns_steps; ++it) {
+            cta_gemm(true, false, n, 1.0, d.V, d.V, d.Y, Xs, Ys);
+            for (int e = threadIdx.x; e < n * n; e += BT) {
+                int r = e % n, c = e / n;
+                d.Y[e] = ((r == c) ? 3.0 : 0.0) - d.Y[e];
+            }
+            __syncthreads();
+            cta_gemm(false, false, n, 0.5, d.V, d.Y, d.T, Xs, Ys);
+            for (int e = threadIdx.x; e < n * n; e += BT) d.V[e] = d.T[e];
+            __syncthreads();
+        }
+        cta_gemm(false, false, n, 1.0, d.Ain, d.V, d.T, Xs, Ys);
+        cta_gemm(true, false, n, 1.0, d.V, d.T, d.A, Xs, Ys);
+        for (int e = threadIdx.x; e < n * n; e += BT) {
+            int r = e % n, c = e / n;
+            if (r < c) {
+                double v = 0.5 * (d.A[r + c * n] + d.A[c + r * n]);
+                d.A[r + c * n] = v;
+                d.A[c + r * n] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace pjac
+
+using namespace pjac;
+
+struct BatchState {
+    void* dbuf = nullptr;     // device: descriptors, order, counters, per-problem workspace
+    size_t dbytes = 0;
+    void* hbuf = nullptr;     // pinned host staging
+    size_t hbytes = 0;
+};
+
+// The batched workspace lives in a handle-independent cache keyed by the
+// handle pointer (kept simple: one per handle, grown on demand).
+#include <mutex>
+#include <unordered_map>
+static std::mutex g_bmu;
+static std::unordered_map<const void*, BatchState> g_bstate;
+
+void pjac_batched_release(const void* h) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bstate.find(h);
+    if (it == g_bstate.end()) return;
+    if (it->second.dbuf) cudaFree(it->second.dbuf);
+    if (it->second.hbuf) cudaFreeHost(it->second.hbuf);
+    g_bstate.erase(it);
+}
+
+static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+namespace pjac {
+int handle_opts(const pjac_handle* h, pjac_opts* o);
+}
+
+extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_off, const double* A,
+                                  const int64_t* w_off, double* W, const int64_t* v_off, double* V,
+                                  pjac_pivot pivot, double tol, pjac_info* infos, void* stream) {
+    if (!h || !n || !a_off || !A || !w_off || !W || !infos) return set_err(PJAC_EINVAL, "NULL argument");
+    if (V && !v_off) return set_err(PJAC_EINVAL, "v_off is NULL while V is not");
+    if (nb < 1) return set_err(PJAC_EINVAL, "nb = %d < 1", nb);
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    pjac_opts opts;
+    handle_opts(h, &opts);
+    if (opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
+        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+    int max_n = 0;
+    size_t ws = 0;
+    for (int p = 0; p < nb; ++p) {
+        if (n[p] < 2 || n[p] > 1024) return set_err(PJAC_EINVAL, "n[%d] = %d outside [2, 1024]", p, n[p]);
+        if (a_off[p] < 0 || w_off[p] < 0 || (V && v_off[p] < 0)) return set_err(PJAC_EINVAL, "negative offset");
+        max_n = std::max(max_n, n[p]);
+        size_t nn = (size_t)n[p] * n[p];
+        ws += a256(nn * 8) * 4 + a256((size_t)n[p] * 8) + a256(nn * 4) * 2 + a256(sizeof(DevInfo));
+    }
+    size_t hdr = a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb) + 256;
+    size_t need = hdr + ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_bmu);
+    BatchState& bs = g_bstate[h];
+    if (bs.dbytes < need) {
+        if (bs.dbuf) cudaFree(bs.dbuf);
+        bs.dbuf = nullptr;
+        bs.dbytes = 0;
+        cudaError_t e = cudaMalloc(&bs.dbuf, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(PJAC_ENOMEM, "batched workspace of %zu bytes: %s", need, cudaGetErrorString(e));
+        }
+        bs.dbytes = need;
+    }
+    size_t hneed = a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb);
+    if (bs.hbytes < hneed) {
+        if (bs.hbuf) cudaFreeHost(bs.hbuf);
+        bs.hbuf = nullptr;
+        bs.hbytes = 0;
+        cudaError_t e = cudaMallocHost(&bs.hbuf, hneed);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(PJAC_ENOMEM, "pinned staging of %zu bytes: %s", hneed, cudaGetErrorString(e));
+        }
+        bs.hbytes = hneed;
+    }
+    // The staging buffer may still be read by an earlier call's copy.
+    cudaError_t e0 = cudaStreamSynchronize(st);
+    if (e0 != cudaSuccess) return cuda_err(e0, "cudaStreamSynchronize");
+    char* dbase = static_cast<char*>(bs.dbuf);
+    BatchDesc* d_desc = reinterpret_cast<BatchDesc*>(dbase);
+    int* d_order = reinterpret_cast<int*>(dbase + a256(sizeof(BatchDesc) * nb));
+    int* d_counters = reinterpret_cast<int*>(dbase + a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb));
+    BatchDesc* h_desc = static_cast<BatchDesc*>(bs.hbuf);
+    int* h_order = reinterpret_cast<int*>(static_cast<char*>(bs.hbuf) + a256(sizeof(BatchDesc) * nb));
+    char* p = dbase + hdr;
+    for (int q = 0; q < nb; ++q) {
+        size_t m = (size_t)n[q], nn = m * m;
+        BatchDesc d;
+        memset(&d, 0, sizeof(d));
+        d.Ain = A + a_off[q];
+        d.A = reinterpret_cast<double*>(p); p += a256(nn * 8);
+        d.V = reinterpret_cast<double*>(p); p += a256(nn * 8);
+        d.T = reinterpret_cast<double*>(p); p += a256(nn * 8);
+        d.Y = reinterpret_cast<double*>(p); p += a256(nn * 8);
+        d.Wd = reinterpret_cast<double*>(p); p += a256(m * 8);
+        d.A32 = reinterpret_cast<float*>(p); p += a256(nn * 4);
+        d.Q32 = reinterpret_cast<float*>(p); p += a256(nn * 4);
+        d.info = reinterpret_cast<DevInfo*>(p); p += a256(sizeof(DevInfo));
+        d.Wout = W + w_off[q];
+        d.Vout = V ? V + v_off[q] : nullptr;
+        d.n = (int)m;
+        h_desc[q] = d;
+        h_order[q] = q;
+    }
+    std::stable_sort(h_order, h_order + nb, [&](int x, int y) { return n[x] > n[y]; });
+    cudaError_t e;
+#define BK(call) do { e = (call); if (e != cudaSuccess) return cuda_err(e, #call); } while (0)
+    BK(cudaMemcpyAsync(d_desc, h_desc, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, st));
+    BK(cudaMemcpyAsync(d_order, h_order, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    BK(cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), st));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int ctas = std::min(nb, sms * 2);
+    size_t smem32 = (size_t)2 * SMEM_N32 * SMEM_N32 * sizeof(float);
+    BK(cudaFuncSetAttribute(b_diag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 30);
+    BK(cudaGetLastError());
+    int ns = opts.ns_steps;
+    b_precond_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 1, ns);
+    BK(cudaGetLastError());
+    long long budget = (long long)((opts.time_budget_s > 0 ? opts.time_budget_s : 600.0) * 2.2e9);
+    BK(launch_jacobi_batched(d_desc, nb, d_order, d_counters + 2, (int)pivot, (int)opts.stop, tol, 25, budget,
+                             max_n, std::min(nb, sms * 2), st));
+    BK(launch_readout_batched(d_desc, nb, max_n, st));
+    BK(launch_info_batched(d_desc, nb, infos, st));
+#undef BK
+    return PJAC_OK;
+}

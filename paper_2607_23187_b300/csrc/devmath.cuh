@@ -1,0 +1,147 @@
+// Device arithmetic of the Jacobi step (Shao & Nakatsukasa, Sec. 2, Eq. (1.1)).
+//
+// Every FP64 operation below is written with an explicit rounding intrinsic
+// (__dadd_rn, __dmul_rn, __fma_rn, __dsqrt_rn, __ddiv_rn), so the result does
+// not depend on compiler contraction: the rotation, the updated entries and
+// the gap score are the IEEE-rounded values of the stated expressions.
+//
+// Expressions (the paper gives the rotation only as "compute c and s such
+// that G_ij^T A_ij G_ij is diagonal"; the standard symmetric 2x2 Schur form
+// with |theta| <= pi/4 is used):
+//   d   = a_ii - a_jj,  q = a_ij,  q2 = q*q
+//   den = |d| + sqrt(d*d + 4*q2)
+//   L   = (2*q2) / den                                  (Eq. (1.1))
+//   t   = (2|q|) / den, negated when d != 0 and sign(d) != sign(q)
+//   c   = den / sqrt(den*den + 4*q2)   (= 1/sqrt(1+t^2)),  s = t*c
+//   a_ii' = fma(t, q, a_ii),  a_jj' = fma(-t, q, a_jj),  a_ij' = 0
+//   x' = fma(c, x, s*y),  y' = fma(c, y, -(s*x))   for (a_ki, a_kj), (v_ki, v_kj)
+// When max(|d|,|q|) lies outside [2^-500, 2^500] both are first scaled by the
+// exact power of two 2^-ilogb(max) (L is homogeneous of degree 1, t and c of
+// degree 0).
+#pragma once
+#include <cstdint>
+#include <climits>
+
+namespace pjac {
+
+__device__ __forceinline__ int scale_exp(double d, double q) {
+    double m = fmax(fabs(d), fabs(q));
+    if (m > 0x1p+500 || m < 0x1p-500) return ilogb(m);
+    return 0;
+}
+
+// Eq. (1.1) for diagonal entries dii, djj and off-diagonal q.
+__device__ __forceinline__ double gap_exact(double dii, double djj, double q) {
+    if (q == 0.0) return 0.0;
+    double d = __dadd_rn(dii, -djj);
+    int e = scale_exp(d, q);
+    if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
+    double q2 = __dmul_rn(q, q);
+    double r = __dsqrt_rn(__dadd_rn(__dmul_rn(d, d), __dmul_rn(4.0, q2)));
+    double den = __dadd_rn(fabs(d), r);
+    double l = __ddiv_rn(__dmul_rn(2.0, q2), den);
+    if (e != 0) l = ldexp(l, e);
+    return l;
+}
+
+struct Rot { double c, s, t; };
+
+__device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
+    Rot r;
+    if (q == 0.0) { r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
+    double d = __dadd_rn(dii, -djj);
+    int e = scale_exp(d, q);
+    if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
+    double q2 = __dmul_rn(q, q);
+    double q4 = __dmul_rn(4.0, q2);
+    double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(d, d), q4));
+    double den = __dadd_rn(fabs(d), rr);
+    double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
+    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    double c = __ddiv_rn(den, __dsqrt_rn(__dadd_rn(__dmul_rn(den, den), q4)));
+    r.t = t;
+    r.c = c;
+    r.s = __dmul_rn(t, c);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Screen keys.  Selecting the pivot needs the exact argmax of the FP64
+// scores (ties to the smallest index), but an FP64 square root and division
+// per entry are expensive.  Entries are first ranked by a 32-bit integer key
+// computed with integer and FP32 instructions; only entries whose key lies
+// within KEY_TIE of the best key are evaluated exactly.
+//
+// Gap rule: key = floor(2^20 * log2(L~)) with |log2 L~ - log2 L| <= 2^-16
+// (mantissas truncated to 23 bits: 2^-23 relative each; a handful of FP32
+// roundings; __log2f within 2 ulp of a result of magnitude <= 64; the
+// asymptotic forms below are exact to 2^-118).  KEY_TIE = 2^20 * 2^-10, far
+// above twice that bound, so an entry whose key is more than KEY_TIE below
+// the best key has a strictly smaller FP64 score.  When the best key is in
+// the range where FP64 scores are subnormal (L < 2^-1060) every entry is
+// evaluated exactly.
+// Greedy rule: key = high 32 bits of |x| (monotone in |x|); entries with the
+// same key are compared on the full |x|.
+// ---------------------------------------------------------------------------
+constexpr int KEY_NONE = INT_MIN;          // no candidate
+constexpr int KEY_ZERO = INT_MIN + 1;      // x == 0: score exactly 0
+constexpr int KEY_GAP_TIE = 1 << 10;
+constexpr int KEY_SUB = -1060 * (1 << 20); // below: FP64 gap scores may be subnormal
+
+__device__ __forceinline__ float mant23(unsigned long long b) {
+    return __int_as_float(0x3f800000u | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
+__device__ __forceinline__ int gap_key(double x, double dd) {
+    unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    if (bx == 0) return KEY_ZERO;
+    unsigned long long bd = (unsigned long long)__double_as_longlong(dd) & 0x7fffffffffffffffULL;
+    int ex = (int)(bx >> 52), ed = (int)(bd >> 52);
+    int adj = 0;
+    if (ex == 0 || (ed == 0 && bd != 0)) {
+        // subnormal operand: scale both by 2^64 (exact), remember the shift
+        bx = (unsigned long long)__double_as_longlong(__dmul_rn(fabs(x), 0x1p64));
+        bd = (unsigned long long)__double_as_longlong(__dmul_rn(fabs(dd), 0x1p64));
+        ex = (int)(bx >> 52);
+        ed = (int)(bd >> 52);
+        adj = 64;
+    }
+    float mx = mant23(bx);
+    int exu = ex - 1023 - adj;
+    int ip;
+    float f;
+    if (bd == 0) {
+        ip = exu;
+        f = __log2f(mx);
+    } else {
+        float md = mant23(bd);
+        int e = ed - ex;
+        if (e >= 60) {             // L ~ x^2/|d|
+            ip = 2 * exu - (ed - 1023 - adj);
+            f = __log2f(__fdiv_rn(mx * mx, md));
+        } else if (e <= -60) {     // L ~ |x|
+            ip = exu;
+            f = __log2f(mx);
+        } else {
+            float rho = __fdiv_rn(md, mx) * __int_as_float((e + 127) << 23);
+            float g = __fdiv_rn(2.0f, rho + __fsqrt_rn(__fmaf_rn(rho, rho, 4.0f)));
+            ip = exu;
+            f = __log2f(mx * g);
+        }
+    }
+    if (ip < -2040) ip = -2040;
+    return ip * (1 << 20) + __float2int_rd(f * 1048576.0f);
+}
+
+__device__ __forceinline__ int greedy_key(double x) {
+    unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    return (int)(bx >> 32);
+}
+
+// Order-preserving 64-bit integer image of a double (for sorting W).
+__device__ __forceinline__ unsigned long long order_key(double w) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(w);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+}  // namespace pjac

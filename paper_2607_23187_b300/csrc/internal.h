@@ -1,0 +1,94 @@
+// Internal declarations shared by the CUDA translation units of libpjac.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/pjac.h"
+
+namespace pjac {
+
+// Device-side report of one Jacobi solve (written by the kernel).
+struct DevInfo {
+    long long rotations;
+    long long sweeps;      // cyclic: sweeps started
+    double off;            // off(A) at exit (absolute)
+    double normf;          // ||A1||_F at entry
+    double max_score;      // last selected score
+    int status;            // pjac_status
+    int n;
+};
+
+struct JacArgs {
+    double* A;             // working matrix, overwritten (column-major == row-major, symmetric)
+    long long lda;
+    double* V;             // accumulated V (column-major), may be null
+    long long ldv;
+    double* Wd;            // out: final diagonal (unsorted), n
+    int n;
+    int pivot;             // pjac_pivot
+    int stop;              // pjac_stop
+    double tol;
+    long long max_rot;
+    long long check_every;
+    long long budget_cycles;
+    DevInfo* info;
+};
+
+// One problem of the batched form, as the device sees it.  All matrices
+// have leading dimension n.
+struct BatchDesc {
+    const double* Ain;     // caller's A (read only)
+    double* A;             // A1 working copy, overwritten by the iteration
+    double* V;             // Q, then the accumulated V
+    double* T;             // product temporaries
+    double* Y;
+    double* Wd;            // unsorted diagonal
+    float* A32;            // FP32 diagonaliser state (used when n > 128)
+    float* Q32;            // FP32 eigenvector estimate Q0
+    double* Wout;          // caller's W of this problem
+    double* Vout;          // caller's V of this problem (may be null)
+    DevInfo* info;
+    int n;
+    int pad;
+};
+
+// jacobi.cu
+cudaError_t launch_jacobi(const JacArgs& a, int cluster, cudaStream_t st);
+int jacobi_auto_cluster(int n);
+cudaError_t launch_jacobi_batched(const BatchDesc* d_desc, int nb, const int* d_order,
+                                  int* d_counter, int pivot, int stop, double tol,
+                                  long long max_rot_per_n2, long long budget_cycles, int max_n,
+                                  int ctas, cudaStream_t st);
+cudaError_t launch_readout(const double* Wd, const double* Vws, long long ldvws, int n,
+                           double* W, double* V, long long ldv, int* rank_ws, cudaStream_t st);
+cudaError_t launch_readout_batched(const BatchDesc* d_desc, int nb, int max_n, cudaStream_t st);
+cudaError_t launch_info_batched(const BatchDesc* d_desc, int nb, pjac_info* infos, cudaStream_t st);
+cudaError_t launch_info_single(const DevInfo* src, pjac_info* dst, cudaStream_t st);
+int solve_async_dev(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol, double* W,
+                    double* V, int ldv, pjac_info* dinfo, cudaStream_t st);
+
+// gemm.cu (transform and Newton--Schulz)
+cudaError_t gemm_f64(bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+                     long long lda, const double* B, long long ldb, double beta, double* C,
+                     long long ldc, cudaStream_t st);
+cudaError_t symmetrize(double* A, long long lda, int n, cudaStream_t st);
+cudaError_t copy_f32_to_f64(const float* src, long long lds, double* dst, long long ldd, int n,
+                            cudaStream_t st);
+cudaError_t copy_f64(const double* src, long long lds, double* dst, long long ldd, int m, int n,
+                     cudaStream_t st);
+cudaError_t set_identity(double* dst, long long ldd, int n, cudaStream_t st);
+cudaError_t three_i_minus(double* Y, long long ldy, int n, cudaStream_t st);
+cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cudaStream_t st);
+
+// Split-precision products on the tensor cores (BF16 slices, FP32 accumulation).
+cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+                            long long lda, const double* B, long long ldb, double beta, double* C,
+                            long long ldc, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t gemm_split_bf16_ws(int m, int n, int k);
+
+// diag32.cu: FP32 parallel-order Jacobi diagonalisation of fl32(A); Q0 out (ld n)
+cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
+                      int max_sweeps, cudaStream_t st);
+size_t diag_fp32_ws_floats(int n);
+
+}  // namespace pjac

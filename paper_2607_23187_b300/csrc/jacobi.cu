@@ -1,0 +1,867 @@
+// Jacobi iteration on the preconditioned matrix (Shao & Nakatsukasa,
+// Algorithm 1, Sec. 2; pivot rules of Sec. 1 and Eq. (1.1); O(n) score
+// update of Sec. 3.2; Theorem 1 stop of Sec. 3.1).
+//
+// One problem is solved by a cluster of P CTAs (P = 1 for small orders and
+// for the batched form).  CTA c owns the index range K_c; for every rotation
+// (i,j) it
+//   1. rotates the entries (k,i),(k,j) and their mirrors (i,k),(j,k) for
+//      k in K_c, and the entries (k,i),(k,j) of V,
+//   2. scores the new entries: its own rows k compare their cached best
+//      entry with (k,i),(k,j) (rows whose best sat in column i or j are
+//      rescanned), and the new rows i and j are scored over K_c,
+//   3. publishes three candidates (its best own row, its part of row i, its
+//      part of row j) in shared memory; one cluster barrier later every CTA
+//      reads all P slots through DSMEM and makes the same selection.
+// Scores are ranked by integer keys; entries whose keys are within the tie
+// band are compared on their exact FP64 scores, so the pivot is the exact
+// argmax of the FP64 scores with ties to the smallest (i,j).
+//
+// A is read and written with ld/st.global.cg (L2), because entries of a row
+// are written by several CTAs between cluster barriers.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <climits>
+#include "devmath.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace pjac {
+
+constexpr int NT = 256;     // threads per CTA
+constexpr int MAXR = 4;     // owned indices per thread (m <= NT * MAXR)
+
+struct Cand {
+    int key, row, col, pad;
+    double x;               // the entry a_row,col
+    double ex;              // exact score (gap) if >= 0, else not yet computed
+};
+
+struct Slot {
+    Cand loc, pi, pj;
+    double sum;
+    int flags, pad;
+};
+
+struct Sh {
+    int wkey[NT / 32];
+    Cand wc[NT / 32];
+    double wsum[NT / 32];
+    Cand out;
+    Slot slots[2];
+    Cand sel;
+    double c, s, t, dii, djj, q;
+    double normf, thr, eps_li, scale;
+    int pi, pj, nresc, decision;
+    int key_eps, pad2;
+};
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg(double* p, double v) { __stcg(p, v); }
+
+__device__ __forceinline__ Cand no_cand() {
+    Cand c;
+    c.key = KEY_NONE; c.row = -1; c.col = -1; c.pad = 0; c.x = 0.0; c.ex = -1.0;
+    return c;
+}
+
+__device__ __forceinline__ int entry_key(int pivot, double x, double dd) {
+    return pivot == PJAC_PIVOT_GREEDY ? greedy_key(x) : gap_key(x, dd);
+}
+
+// Exact score of a candidate (gap: Eq. (1.1) in FP64; greedy: |x|).
+__device__ __forceinline__ double cand_value(Cand& c, int pivot, const double* diag) {
+    if (pivot == PJAC_PIVOT_GREEDY) return fabs(c.x);
+    if (c.ex < 0.0) c.ex = gap_exact(diag[c.row], diag[c.col], c.x);
+    return c.ex;
+}
+
+__device__ __forceinline__ bool exact_better(double va, const Cand& a, double vb, const Cand& b) {
+    if (va != vb) return va > vb;
+    if (a.row != b.row) return a.row < b.row;
+    return a.col < b.col;
+}
+
+// Is a strictly better than b (larger score, then smaller (row, col))?
+__device__ __forceinline__ bool better(Cand& a, Cand& b, int pivot, const double* diag) {
+    if (a.key == KEY_NONE) return false;
+    if (b.key == KEY_NONE) return true;
+    if (pivot == PJAC_PIVOT_GREEDY) {
+        if (a.key != b.key) return a.key > b.key;
+    } else {
+        int km = max(a.key, b.key);
+        if (km >= KEY_SUB) {
+            long long d = (long long)a.key - (long long)b.key;
+            if (d > KEY_GAP_TIE) return true;
+            if (d < -KEY_GAP_TIE) return false;
+        }
+    }
+    double va = cand_value(a, pivot, diag), vb = cand_value(b, pivot, diag);
+    return exact_better(va, a, vb, b);
+}
+
+__device__ __forceinline__ int block_max_int(int v, Sh& sh) {
+    int w = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) sh.wkey[threadIdx.x >> 5] = w;
+    __syncthreads();
+    int r = sh.wkey[0];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) r = max(r, sh.wkey[k]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ Cand shfl_cand(const Cand& c, int src) {
+    Cand o;
+    o.key = __shfl_sync(0xffffffffu, c.key, src);
+    o.row = __shfl_sync(0xffffffffu, c.row, src);
+    o.col = __shfl_sync(0xffffffffu, c.col, src);
+    o.pad = 0;
+    o.x = __shfl_sync(0xffffffffu, c.x, src);
+    o.ex = __shfl_sync(0xffffffffu, c.ex, src);
+    return o;
+}
+
+// Block-wide exact argmax of one candidate per thread.  Phase 1 takes the
+// maximum key; phase 2 (only when several threads are within the tie band)
+// evaluates the contenders exactly.  Uniform call (all threads).
+__device__ Cand block_select(Cand mine, int pivot, const double* diag, Sh& sh) {
+    int kmax = block_max_int(mine.key, sh);
+    if (kmax == KEY_NONE) return no_cand();
+    bool exact_all = (pivot != PJAC_PIVOT_GREEDY) && kmax < KEY_SUB;
+    int tie = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_GAP_TIE;
+    bool cont = mine.key != KEY_NONE && (exact_all || (long long)mine.key >= (long long)kmax - tie);
+    int nc = __syncthreads_count(cont);
+    if (nc == 1) {
+        if (cont) sh.out = mine;
+        __syncthreads();
+        Cand r = sh.out;
+        __syncthreads();
+        return r;
+    }
+    double v = -2.0;
+    if (cont) v = cand_value(mine, pivot, diag);
+    int lane = threadIdx.x & 31;
+    // warp argmax on (v desc, row asc, col asc)
+    double bv = v;
+    int br = mine.row, bc = mine.col, bl = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        int orr = __shfl_xor_sync(0xffffffffu, br, off);
+        int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        bool take = (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
+        if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
+    }
+    if (lane == bl) {
+        Cand w = mine;
+        if (bv < -1.0) w.key = KEY_NONE;
+        sh.wc[threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Cand best = no_cand();
+        double vb = -2.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            Cand c = sh.wc[w];
+            if (c.key == KEY_NONE) continue;
+            double vc = cand_value(c, pivot, diag);
+            if (best.key == KEY_NONE || exact_better(vc, c, vb, best)) { best = c; vb = vc; }
+        }
+        sh.out = best;
+    }
+    __syncthreads();
+    Cand r = sh.out;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_sum(double v, Sh& sh) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) sh.wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) r += sh.wsum[k];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_maxabs(double v, Sh& sh) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) sh.wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) r = fmax(r, sh.wsum[k]);
+    __syncthreads();
+    return r;
+}
+
+// Key of a positive value on the gap-key scale (floor(2^20 log2 v) within
+// the same error band).
+__device__ __forceinline__ int value_key(double v) {
+    if (v <= 0.0) return KEY_ZERO;
+    return gap_key(v, 0.0);
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ void cta_exchange_sync() {
+    if (CLUSTER) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    } else {
+        __syncthreads();
+    }
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ const Slot* peer_slot(Sh& sh, int par, int r) {
+    if (CLUSTER) {
+        cg::cluster_group cl = cg::this_cluster();
+        return cl.map_shared_rank(&sh.slots[par], r);
+    }
+    return &sh.slots[par];
+}
+
+// Rescan row k (block-wide): best entry over l != k.
+__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh) {
+    const double* row = a.A + (long long)k * a.lda;
+    double dk = diag[k];
+    Cand best = no_cand();
+    for (int l0 = threadIdx.x; l0 < a.n; l0 += 4 * NT) {
+        double xs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int l = l0 + u * NT;
+            xs[u] = (l < a.n) ? ldcg(row + l) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int l = l0 + u * NT;
+            if (l >= a.n || l == k) continue;
+            Cand c;
+            c.row = k; c.col = l; c.pad = 0; c.x = xs[u]; c.ex = -1.0;
+            c.key = entry_key(a.pivot, xs[u], a.pivot == PJAC_PIVOT_GREEDY ? 0.0 : __dadd_rn(dk, -diag[l]));
+            if (better(c, best, a.pivot, diag)) best = c;
+        }
+    }
+    return block_select(best, a.pivot, diag, sh);
+}
+
+// off(A)^2 * 2^-2e over the owned rows, e = ilogb(||A1||_F) (as the oracle).
+__device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, Sh& sh) {
+    double acc = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const double* row = a.A + (long long)k * a.lda;
+        for (int l = threadIdx.x; l < a.n; l += NT) {
+            if (l == k) continue;
+            double x = __dmul_rn(ldcg(row + l), scale);
+            acc = __fma_rn(x, x, acc);
+        }
+    }
+    return block_sum(acc, sh);
+}
+
+// Solve one problem.  rank/P: this CTA's rank in the cluster and the
+// cluster size.  Shared arrays: diag[n], cache[m], resc[m].
+template <bool CLUSTER>
+__device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double* diag,
+                               Cand* cache, int* resc) {
+    const int n = a.n;
+    const int tid = threadIdx.x;
+    const int mchunk = (n + P - 1) / P;
+    const int k0 = min(n, rank * mchunk);
+    const int k1 = min(n, k0 + mchunk);
+    const int pivot = a.pivot;
+    long long start = clock64();
+
+    for (int k = tid; k < n; k += NT) diag[k] = ldcg(a.A + (long long)k * a.lda + k);
+
+    // ||A1||_F with the oracle's scaling: max |a|, then sum of (a 2^-e)^2.
+    double mx = 0.0;
+    for (int k = k0; k < k1; ++k)
+        for (int l = tid; l < n; l += NT) mx = fmax(mx, fabs(ldcg(a.A + (long long)k * a.lda + l)));
+    mx = block_maxabs(mx, sh);
+    int par = 0;
+    if (tid == 0) sh.slots[par].sum = mx;
+    cta_exchange_sync<CLUSTER>();
+    if (tid == 0) {
+        double g = 0.0;
+        for (int r = 0; r < P; ++r) g = fmax(g, peer_slot<CLUSTER>(sh, par, r)->sum);
+        sh.scale = (g > 0.0) ? ldexp(1.0, -ilogb(g)) : 1.0;
+        sh.normf = g;   // temporary: max |a|
+    }
+    par ^= 1;
+    __syncthreads();
+    {
+        double acc = 0.0;
+        double scl = sh.scale;
+        for (int k = k0; k < k1; ++k)
+            for (int l = tid; l < n; l += NT) {
+                double x = __dmul_rn(ldcg(a.A + (long long)k * a.lda + l), scl);
+                acc = __fma_rn(x, x, acc);
+            }
+        acc = block_sum(acc, sh);
+        if (tid == 0) sh.slots[par].sum = acc;
+    }
+    cta_exchange_sync<CLUSTER>();
+    if (tid == 0) {
+        double g = 0.0;
+        for (int r = 0; r < P; ++r) g += peer_slot<CLUSTER>(sh, par, r)->sum;
+        double maxa = sh.normf;
+        double nf = (maxa > 0.0) ? ldexp(sqrt(g), ilogb(maxa)) : 0.0;
+        sh.normf = nf;
+        sh.thr = a.tol * nf;
+        sh.eps_li = a.tol * nf / (2.0 * (double)n * (double)(n - 1));
+        sh.scale = (nf > 0.0) ? ldexp(1.0, -ilogb(nf)) : 1.0;
+        sh.key_eps = value_key(sh.eps_li);
+    }
+    par ^= 1;
+    __syncthreads();
+
+    long long rot = 0, sweeps = 0;
+    int status = PJAC_ENOCONV;
+    double last_score = 0.0;
+    const long long ce = a.check_every > 0 ? a.check_every : n;
+
+    // ---- convergence test (collective over the cluster) ----
+    auto offdiag_check = [&](bool& stop_now) {
+        double part = owned_offsum(a, k0, k1, sh.scale, sh);
+        if (tid == 0) {
+            sh.slots[par].sum = part;
+            sh.slots[par].flags = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
+        }
+        cta_exchange_sync<CLUSTER>();
+        if (tid == 0) {
+            double g = 0.0;
+            for (int r = 0; r < P; ++r) g += peer_slot<CLUSTER>(sh, par, r)->sum;
+            double off = (sh.normf > 0.0) ? __dmul_rn(sqrt(g), 1.0 / sh.scale) : 0.0;
+            int dec = 0;
+            if (peer_slot<CLUSTER>(sh, par, 0)->flags & 1) dec = 2;
+            else if (a.stop == PJAC_STOP_OFFDIAG && off <= sh.thr) dec = 1;
+            sh.decision = dec;
+        }
+        par ^= 1;
+        __syncthreads();
+        stop_now = sh.decision != 0;
+        if (sh.decision == 1) status = PJAC_OK;
+        if (sh.decision == 2) status = PJAC_ETIMEOUT;
+    };
+
+    // ---- rotate rows/cols i,j for the owned indices, and V ----
+    auto rotate_owned = [&](int i, int j, const double c, const double s, const double dii_new,
+                            const double djj_new, bool score, Cand& pI, Cand& pJ) {
+        double* Ai = a.A + (long long)i * a.lda;
+        double* Aj = a.A + (long long)j * a.lda;
+        const int cmin = min(i, j), cmax = max(i, j);
+        const double di = diag[i], dj = diag[j];   // already updated
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            int k = k0 + tid + r * NT;
+            if (k >= k1) break;
+            if (a.V) {
+                double* Vi = a.V + (long long)i * a.ldv;
+                double* Vj = a.V + (long long)j * a.ldv;
+                double vx = Vi[k], vy = Vj[k];
+                Vi[k] = __fma_rn(c, vx, __dmul_rn(s, vy));
+                Vj[k] = __fma_rn(c, vy, -__dmul_rn(s, vx));
+            }
+            if (k == i) {
+                stcg(Ai + i, dii_new);
+                stcg(Aj + i, 0.0);
+                stcg(Ai + j, 0.0);
+                if (score) {
+                    Cand z; z.key = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO; z.row = j; z.col = i;
+                    z.pad = 0; z.x = 0.0; z.ex = -1.0;
+                    if (better(z, pJ, pivot, diag)) pJ = z;
+                }
+                continue;
+            }
+            if (k == j) {
+                stcg(Aj + j, djj_new);
+                stcg(Ai + j, 0.0);
+                stcg(Aj + i, 0.0);
+                if (score) {
+                    Cand z; z.key = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO; z.row = i; z.col = j;
+                    z.pad = 0; z.x = 0.0; z.ex = -1.0;
+                    if (better(z, pI, pivot, diag)) pI = z;
+                }
+                continue;
+            }
+            double x = ldcg(Ai + k), y = ldcg(Aj + k);
+            double xn = __fma_rn(c, x, __dmul_rn(s, y));
+            double yn = __fma_rn(c, y, -__dmul_rn(s, x));
+            double* Ak = a.A + (long long)k * a.lda;
+            stcg(Ai + k, xn);
+            stcg(Aj + k, yn);
+            stcg(Ak + i, xn);
+            stcg(Ak + j, yn);
+            if (!score) continue;
+            double dk = diag[k];
+            int kx, ky;
+            if (pivot == PJAC_PIVOT_GREEDY) {
+                kx = greedy_key(xn);
+                ky = greedy_key(yn);
+            } else {
+                kx = gap_key(xn, __dadd_rn(dk, -di));
+                ky = gap_key(yn, __dadd_rn(dk, -dj));
+            }
+            Cand ci; ci.key = kx; ci.row = i; ci.col = k; ci.pad = 0; ci.x = xn; ci.ex = -1.0;
+            Cand cj; cj.key = ky; cj.row = j; cj.col = k; cj.pad = 0; cj.x = yn; cj.ex = -1.0;
+            if (better(ci, pI, pivot, diag)) pI = ci;
+            if (better(cj, pJ, pivot, diag)) pJ = cj;
+            // own row k: compare with its cached best, or rescan
+            Cand cur = cache[k - k0];
+            if (cur.col == i || cur.col == j) {
+                int slot = atomicAdd(&sh.nresc, 1);
+                resc[slot] = k;
+            } else {
+                Cand e1, e2;
+                e1.row = k; e1.pad = 0; e1.ex = -1.0;
+                e2 = e1;
+                if (cmin == i) { e1.col = i; e1.key = kx; e1.x = xn; e2.col = j; e2.key = ky; e2.x = yn; }
+                else           { e1.col = j; e1.key = ky; e1.x = yn; e2.col = i; e2.key = kx; e2.x = xn; }
+                (void)cmax;
+                if (better(e1, cur, pivot, diag)) cur = e1;
+                if (better(e2, cur, pivot, diag)) cur = e2;
+                cache[k - k0] = cur;
+            }
+        }
+    };
+
+    if (pivot == PJAC_PIVOT_CYCLIC) {
+        bool stop_now = false;
+        for (;;) {
+            offdiag_check(stop_now);
+            if (stop_now) break;
+            sweeps++;
+            bool any = false;
+            bool budget = false;
+            for (int i = 0; i < n - 1 && !budget; ++i) {
+                for (int j = i + 1; j < n; ++j) {
+                    double q = ldcg(a.A + (long long)i * a.lda + j);
+                    if (q == 0.0) continue;
+                    if (rot >= a.max_rot) { budget = true; status = PJAC_ENOCONV; break; }
+                    if (tid == 0) {
+                        Rot rp = rot_params(diag[i], diag[j], q);
+                        sh.c = rp.c; sh.s = rp.s;
+                        sh.dii = __fma_rn(rp.t, q, diag[i]);
+                        sh.djj = __fma_rn(-rp.t, q, diag[j]);
+                    }
+                    __syncthreads();
+                    double c = sh.c, s = sh.s, dii = sh.dii, djj = sh.djj;
+                    __syncthreads();
+                    if (tid == 0) { diag[i] = dii; diag[j] = djj; }
+                    __syncthreads();
+                    Cand d1 = no_cand(), d2 = no_cand();
+                    rotate_owned(i, j, c, s, dii, djj, false, d1, d2);
+                    rot++;
+                    any = true;
+                    cta_exchange_sync<CLUSTER>();
+                }
+            }
+            if (budget) break;
+            if (!any) { status = PJAC_OK; break; }
+        }
+        last_score = 0.0;
+    } else {
+        // initial scan (Sec. 3.2: O(n^2) scores once)
+        for (int k = k0; k < k1; ++k) {
+            Cand b = rescan_row(a, k, diag, sh);
+            if (tid == 0) cache[k - k0] = b;
+        }
+        __syncthreads();
+        // first selection
+        {
+            Cand loc = no_cand();
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                int k = k0 + tid + r * NT;
+                if (k >= k1) break;
+                Cand c = cache[k - k0];
+                if (better(c, loc, pivot, diag)) loc = c;
+            }
+            loc = block_select(loc, pivot, diag, sh);
+            if (tid == 0) {
+                sh.slots[par].loc = loc;
+                sh.slots[par].pi = no_cand();
+                sh.slots[par].pj = no_cand();
+            }
+            cta_exchange_sync<CLUSTER>();
+            if (tid == 0) {
+                Cand g = no_cand();
+                for (int r = 0; r < P; ++r) {
+                    Cand c = peer_slot<CLUSTER>(sh, par, r)->loc;
+                    if (better(c, g, pivot, diag)) g = c;
+                }
+                sh.sel = g;
+            }
+            par ^= 1;
+            __syncthreads();
+        }
+        bool stop_now = false;
+        for (;;) {
+            if (rot % ce == 0) {
+                offdiag_check(stop_now);
+                if (stop_now) break;
+            }
+            // decisions on the current selection (thread 0, then broadcast)
+            if (tid == 0) {
+                Cand g = sh.sel;
+                int dec = 0;
+                double v = -1.0;
+                if (g.key == KEY_NONE) dec = 1;   // n < 2
+                else if (pivot == PJAC_PIVOT_GREEDY) {
+                    v = fabs(g.x);
+                    if (v == 0.0) dec = 1;
+                } else {
+                    if (g.key == KEY_ZERO) { v = 0.0; dec = 1; }
+                    else if (g.key < KEY_SUB) { v = cand_value(g, pivot, diag); if (v == 0.0) dec = 1; }
+                    if (!dec && a.stop == PJAC_STOP_LIBOUND) {
+                        long long dk = (long long)g.key - (long long)sh.key_eps;
+                        if (dk <= KEY_GAP_TIE) {
+                            v = cand_value(g, pivot, diag);
+                            if (v <= sh.eps_li) dec = 1;
+                        }
+                    }
+                }
+                if (!dec && rot >= a.max_rot) dec = 3;
+                if (v >= 0.0) sh.q = v;   // remember exact score when known
+                sh.decision = dec;
+                if (!dec) {
+                    int i = min(g.row, g.col), j = max(g.row, g.col);
+                    double q = g.x;
+                    Rot rp = rot_params(diag[i], diag[j], q);
+                    sh.pi = i; sh.pj = j;
+                    sh.c = rp.c; sh.s = rp.s;
+                    sh.dii = __fma_rn(rp.t, q, diag[i]);
+                    sh.djj = __fma_rn(-rp.t, q, diag[j]);
+                    diag[i] = sh.dii;
+                    diag[j] = sh.djj;
+                }
+                sh.nresc = 0;
+            }
+            __syncthreads();
+            if (sh.decision == 1) { status = PJAC_OK; break; }
+            if (sh.decision == 3) { status = PJAC_ENOCONV; break; }
+            const int i = sh.pi, j = sh.pj;
+            const double c = sh.c, s = sh.s, dii = sh.dii, djj = sh.djj;
+            Cand pI = no_cand(), pJ = no_cand();
+            rotate_owned(i, j, c, s, dii, djj, true, pI, pJ);
+            rot++;
+            __syncthreads();
+            // rescans of owned rows whose best was in column i or j
+            const int nr = sh.nresc;
+            for (int r = 0; r < nr; ++r) {
+                int k = resc[r];
+                Cand b = rescan_row(a, k, diag, sh);
+                if (tid == 0) cache[k - k0] = b;
+            }
+            __syncthreads();
+            Cand loc = no_cand();
+#pragma unroll
+            for (int r = 0; r < MAXR; ++r) {
+                int k = k0 + tid + r * NT;
+                if (k >= k1) break;
+                if (k == i || k == j) continue;
+                Cand cc = cache[k - k0];
+                if (better(cc, loc, pivot, diag)) loc = cc;
+            }
+            loc = block_select(loc, pivot, diag, sh);
+            pI = block_select(pI, pivot, diag, sh);
+            pJ = block_select(pJ, pivot, diag, sh);
+            if (tid == 0) {
+                sh.slots[par].loc = loc;
+                sh.slots[par].pi = pI;
+                sh.slots[par].pj = pJ;
+                sh.slots[par].flags = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
+            }
+            cta_exchange_sync<CLUSTER>();
+            if (tid == 0) {
+                Cand bi = no_cand(), bj = no_cand(), g = no_cand();
+                for (int r = 0; r < P; ++r) {
+                    const Slot* ps = peer_slot<CLUSTER>(sh, par, r);
+                    Cand ci = ps->pi, cj = ps->pj;
+                    if (better(ci, bi, pivot, diag)) bi = ci;
+                    if (better(cj, bj, pivot, diag)) bj = cj;
+                }
+                for (int r = 0; r < P; ++r) {
+                    Cand cl = peer_slot<CLUSTER>(sh, par, r)->loc;
+                    if (better(cl, g, pivot, diag)) g = cl;
+                }
+                if (better(bi, g, pivot, diag)) g = bi;
+                if (better(bj, g, pivot, diag)) g = bj;
+                if (i >= k0 && i < k1) cache[i - k0] = bi;
+                if (j >= k0 && j < k1) cache[j - k0] = bj;
+                sh.sel = g;
+                sh.decision = (peer_slot<CLUSTER>(sh, par, 0)->flags & 1) ? 2 : 0;
+            }
+            par ^= 1;
+            __syncthreads();
+            if (sh.decision == 2) { status = PJAC_ETIMEOUT; break; }
+        }
+        if (tid == 0) last_score = sh.sel.key == KEY_NONE ? 0.0 :
+                          (pivot == PJAC_PIVOT_GREEDY ? fabs(sh.sel.x) : cand_value(sh.sel, pivot, diag));
+    }
+
+    // final off(A) and outputs
+    double part = owned_offsum(a, k0, k1, sh.scale, sh);
+    if (tid == 0) sh.slots[par].sum = part;
+    cta_exchange_sync<CLUSTER>();
+    if (tid == 0) {
+        double g = 0.0;
+        for (int r = 0; r < P; ++r) g += peer_slot<CLUSTER>(sh, par, r)->sum;
+        sh.q = (sh.normf > 0.0) ? __dmul_rn(sqrt(g), 1.0 / sh.scale) : 0.0;
+    }
+    // keep peers' shared memory alive until everyone has read it
+    cta_exchange_sync<CLUSTER>();
+    for (int k = k0 + tid; k < k1; k += NT) a.Wd[k] = diag[k];
+    if (rank == 0 && tid == 0 && a.info) {
+        DevInfo inf;
+        inf.rotations = rot;
+        inf.sweeps = sweeps;
+        inf.off = sh.q;
+        inf.normf = sh.normf;
+        inf.max_score = last_score;
+        inf.status = status;
+        inf.n = n;
+        *a.info = inf;
+    }
+}
+
+size_t jacobi_smem_bytes(int n, int P) {
+    int m = (n + P - 1) / P;
+    return (size_t)n * sizeof(double) + (size_t)m * sizeof(Cand) + (size_t)m * sizeof(int) + 16;
+}
+
+template <bool CLUSTER>
+__global__ void __launch_bounds__(NT) jacobi_single_kernel(JacArgs a) {
+    __shared__ Sh sh;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    int P = 1, rank = 0;
+    if (CLUSTER) {
+        cg::cluster_group cl = cg::this_cluster();
+        P = (int)cl.num_blocks();
+        rank = (int)cl.block_rank();
+    }
+    int m = (a.n + P - 1) / P;
+    double* diag = reinterpret_cast<double*>(dyn);
+    Cand* cache = reinterpret_cast<Cand*>(diag + a.n);
+    int* resc = reinterpret_cast<int*>(cache + m);
+    jacobi_problem<CLUSTER>(a, rank, P, sh, diag, cache, resc);
+}
+
+// Batched form: each CTA takes problems from a queue (largest first).
+__global__ void __launch_bounds__(NT) jacobi_batched_kernel(const BatchDesc* desc, int nb,
+                                                           const int* order, int* counter,
+                                                           int pivot, int stop, double tol,
+                                                           long long max_rot_per_n2,
+                                                           long long budget_cycles) {
+    __shared__ Sh sh;
+    __shared__ int next;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        __syncthreads();
+        int t = next;
+        __syncthreads();
+        if (t >= nb) break;
+        BatchDesc d = desc[order[t]];
+        JacArgs a;
+        a.A = d.A; a.lda = d.n; a.V = d.V; a.ldv = d.n; a.Wd = d.Wd; a.n = d.n;
+        a.pivot = pivot; a.stop = stop; a.tol = tol;
+        a.max_rot = max_rot_per_n2 * (long long)d.n * (long long)d.n;
+        a.check_every = d.n; a.budget_cycles = budget_cycles; a.info = d.info;
+        double* diag = reinterpret_cast<double*>(dyn);
+        Cand* cache = reinterpret_cast<Cand*>(diag + d.n);
+        int* resc = reinterpret_cast<int*>(cache + d.n);
+        jacobi_problem<false>(a, 0, 1, sh, diag, cache, resc);
+        __syncthreads();
+    }
+}
+
+int jacobi_auto_cluster(int n) {
+    if (n <= 384) return 1;
+    if (n <= 1024) return 4;
+    if (n <= 2048) return 8;
+    return 16;
+}
+
+cudaError_t launch_jacobi(const JacArgs& a, int P, cudaStream_t st) {
+    if (P < 1) P = 1;
+    int m = (a.n + P - 1) / P;
+    if (m > NT * MAXR) return cudaErrorInvalidValue;
+    size_t smem = jacobi_smem_bytes(a.n, P);
+    if (P == 1) {
+        cudaError_t e = cudaFuncSetAttribute(jacobi_single_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        jacobi_single_kernel<false><<<1, NT, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(jacobi_single_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (P > 8) {
+        e = cudaFuncSetAttribute(jacobi_single_kernel<true>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = P;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(P);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, jacobi_single_kernel<true>, a);
+}
+
+cudaError_t launch_jacobi_batched(const BatchDesc* d_desc, int nb, const int* d_order,
+                                  int* d_counter, int pivot, int stop, double tol,
+                                  long long max_rot_per_n2, long long budget_cycles, int max_n,
+                                  int ctas, cudaStream_t st) {
+    if (max_n > NT * MAXR) return cudaErrorInvalidValue;
+    size_t smem = jacobi_smem_bytes(max_n, 1);
+    cudaError_t e = cudaFuncSetAttribute(jacobi_batched_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    jacobi_batched_kernel<<<ctas, NT, smem, st>>>(d_desc, nb, d_order, d_counter, pivot, stop,
+                                                  tol, max_rot_per_n2, budget_cycles);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Readout: W ascending (ties by index), V's columns in the same order.
+// ---------------------------------------------------------------------------
+__global__ void rank_kernel(const double* Wd, int n, int* rank) {
+    __shared__ unsigned long long tile[256];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long mine = (k < n) ? order_key(Wd[k]) : 0ULL;
+    int r = 0;
+    for (int base = 0; base < n; base += 256) {
+        int l = base + threadIdx.x;
+        tile[threadIdx.x] = (l < n) ? order_key(Wd[l]) : ~0ULL;
+        __syncthreads();
+        int lim = min(256, n - base);
+        for (int u = 0; u < lim; ++u) {
+            unsigned long long o = tile[u];
+            int l2 = base + u;
+            r += (o < mine) || (o == mine && l2 < k);
+        }
+        __syncthreads();
+    }
+    if (k < n) rank[k] = r;
+}
+
+__global__ void gather_kernel(const double* Wd, const double* Vws, long long ldvws, int n,
+                              const int* rank, double* W, double* V, long long ldv) {
+    int col = blockIdx.y;
+    int r = rank[col];
+    if (blockIdx.x == 0 && threadIdx.x == 0) W[r] = Wd[col];
+    if (V == nullptr) return;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x)
+        V[(long long)r * ldv + row] = Vws[(long long)col * ldvws + row];
+}
+
+cudaError_t launch_readout(const double* Wd, const double* Vws, long long ldvws, int n,
+                           double* W, double* V, long long ldv, int* rank_ws, cudaStream_t st) {
+    rank_kernel<<<(n + 255) / 256, 256, 0, st>>>(Wd, n, rank_ws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g((n + 255) / 256, n);
+    gather_kernel<<<g, 256, 0, st>>>(Wd, Vws, ldvws, n, rank_ws, W, V, ldv);
+    return cudaGetLastError();
+}
+
+// Batched readout: one CTA per problem, sort by ranks in shared memory.
+__global__ void readout_batched_kernel(const BatchDesc* desc, int nb) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    int p = blockIdx.x;
+    if (p >= nb) return;
+    BatchDesc d = desc[p];
+    int n = d.n;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(dyn);
+    int* rank = reinterpret_cast<int*>(keys + n);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) keys[k] = order_key(d.Wd[k]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        unsigned long long mine = keys[k];
+        int r = 0;
+        for (int l = 0; l < n; ++l) r += (keys[l] < mine) || (keys[l] == mine && l < k);
+        rank[k] = r;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) d.Wout[rank[k]] = d.Wd[k];
+    if (d.Vout) {
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+            int col = (int)(e / n), row = (int)(e % n);
+            d.Vout[(long long)rank[col] * n + row] = d.V[(long long)col * n + row];
+        }
+    }
+}
+
+cudaError_t launch_readout_batched(const BatchDesc* d_desc, int nb, int max_n, cudaStream_t st) {
+    size_t smem = (size_t)max_n * (sizeof(unsigned long long) + sizeof(int));
+    readout_batched_kernel<<<nb, 256, smem, st>>>(d_desc, nb);
+    return cudaGetLastError();
+}
+
+__global__ void info_batched_kernel(const BatchDesc* desc, int nb, pjac_info* infos) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nb) return;
+    DevInfo d = *desc[p].info;
+    pjac_info o;
+    o.rotations = d.rotations;
+    double pairs = 0.5 * (double)d.n * (double)(d.n - 1);
+    o.sweeps = (d.sweeps > 0) ? (double)d.sweeps : (pairs > 0 ? (double)d.rotations / pairs : 0.0);
+    o.off_rel = d.normf > 0 ? d.off / d.normf : 0.0;
+    o.max_score = d.max_score;
+    o.status = d.status;
+    o.n = d.n;
+    o.ms_precond = 0.f;
+    o.ms_transform = 0.f;
+    o.ms_jacobi = 0.f;
+    infos[p] = o;
+}
+
+__global__ void info_single_kernel(const DevInfo* src, pjac_info* dst) {
+    DevInfo d = *src;
+    pjac_info o;
+    o.rotations = d.rotations;
+    double pairs = 0.5 * (double)d.n * (double)(d.n - 1);
+    o.sweeps = (d.sweeps > 0) ? (double)d.sweeps : (pairs > 0 ? (double)d.rotations / pairs : 0.0);
+    o.off_rel = d.normf > 0 ? d.off / d.normf : 0.0;
+    o.max_score = d.max_score;
+    o.status = d.status;
+    o.n = d.n;
+    o.ms_precond = 0.f;
+    o.ms_transform = 0.f;
+    o.ms_jacobi = 0.f;
+    *dst = o;
+}
+
+cudaError_t launch_info_single(const DevInfo* src, pjac_info* dst, cudaStream_t st) {
+    info_single_kernel<<<1, 1, 0, st>>>(src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_info_batched(const BatchDesc* d_desc, int nb, pjac_info* infos, cudaStream_t st) {
+    info_batched_kernel<<<(nb + 127) / 128, 128, 0, st>>>(d_desc, nb, infos);
+    return cudaGetLastError();
+}
+
+}  // namespace pjac

@@ -1,0 +1,380 @@
+// Serving form: continuous batching of eigenproblems of mixed orders.
+//
+// Requests arrive through pjac_serve_submit (host buffers).  The scheduler
+// (run from submit, poll and progress; no background thread) keeps a FIFO of
+// waiting requests and a set of lanes, each a CUDA stream with its own solver
+// handle.  A free lane takes work as soon as it appears:
+//   - requests of order <= BATCH_MAX_N waiting at that moment are admitted
+//     together as one micro-batch (the batched kernels, one persistent launch
+//     per stage), as many as the device-memory budget allows;
+//   - a larger request takes a lane alone and runs the single-problem path
+//     (cluster-parallel Jacobi).
+// Admission is by device footprint: a request is admitted only while the
+// bytes of all admitted requests stay within the budget.  Work of different
+// lanes overlaps on the device.  A lane's results are copied back on its
+// stream; completion is detected with an event query, and the lane is
+// recycled at once.  Latency = completion detected - submit.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+#include "internal.h"
+
+namespace pjac {
+int set_err(int code, const char* fmt, ...);
+int cuda_err(cudaError_t e, const char* what);
+}
+using namespace pjac;
+
+namespace {
+
+constexpr int BATCH_MAX_N = 256;
+using clk = std::chrono::steady_clock;
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(clk::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t ticket;
+    int n;
+    pjac_pivot pivot;
+    double tol;
+    std::vector<double> a;       // host copy of A (column-major, ld n)
+    double* w_out;
+    double* v_out;
+    int ldv;
+    double t_submit;
+    double t_done;
+    int status = PJAC_PENDING;
+    pjac_info info;
+    size_t footprint;
+};
+
+struct Lane {
+    cudaStream_t st = nullptr;
+    pjac_handle* h = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<Request*> reqs;
+    // device buffers (grown on demand) and pinned host staging
+    double* dA = nullptr; size_t dA_bytes = 0;
+    double* dW = nullptr; size_t dW_bytes = 0;
+    double* dV = nullptr; size_t dV_bytes = 0;
+    pjac_info* dInfo = nullptr; size_t dInfo_bytes = 0;
+    double* hA = nullptr; size_t hA_bytes = 0;
+    double* hW = nullptr; size_t hW_bytes = 0;
+    double* hV = nullptr; size_t hV_bytes = 0;
+    pjac_info* hInfo = nullptr; size_t hInfo_bytes = 0;
+    std::vector<int> ns;
+    std::vector<int64_t> aoff, woff;
+    size_t footprint = 0;
+    int launch_status = PJAC_OK;
+};
+
+template <class T>
+int grow_dev(T*& p, size_t& cur, size_t need) {
+    if (need <= cur) return PJAC_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cur = 0;
+    cudaError_t e = cudaMalloc((void**)&p, need);
+    if (e != cudaSuccess) { cudaGetLastError(); return set_err(PJAC_ENOMEM, "serve: cudaMalloc %zu", need); }
+    cur = need;
+    return PJAC_OK;
+}
+
+template <class T>
+int grow_host(T*& p, size_t& cur, size_t need) {
+    if (need <= cur) return PJAC_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cur = 0;
+    cudaError_t e = cudaMallocHost((void**)&p, need);
+    if (e != cudaSuccess) { cudaGetLastError(); return set_err(PJAC_ENOMEM, "serve: cudaMallocHost %zu", need); }
+    cur = need;
+    return PJAC_OK;
+}
+
+// Device bytes a request holds while admitted: input, outputs and the
+// solver's workspace (about 4 n^2 doubles plus FP32 state).
+size_t request_footprint(int n) {
+    size_t nn = (size_t)n * n;
+    return nn * 8 * 7 + nn * 4 * 6 + (size_t)n * 64 + 4096;
+}
+
+}  // namespace
+
+struct pjac_server {
+    pjac_serve_opts o;
+    std::mutex mu;
+    std::vector<Lane> lanes;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> all;   // queued, running or finished-not-polled
+    uint64_t next_ticket = 1;
+    size_t in_use = 0;
+    int64_t inflight = 0, peak_inflight = 0;
+    size_t peak_hbm = 0;
+    std::vector<double> lat_ms;
+    double first_submit = -1, last_done = -1;
+};
+
+extern "C" void pjac_serve_default_opts(pjac_serve_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->max_slots = 8;
+    o->max_queue = 1 << 16;
+    o->hbm_budget_bytes = (size_t)8 << 30;
+    pjac_default_opts(&o->solver);
+}
+
+extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
+    if (!s) return set_err(PJAC_EINVAL, "s is NULL");
+    *s = nullptr;
+    pjac_serve_opts d;
+    pjac_serve_default_opts(&d);
+    if (o) {
+        d = *o;
+        if (d.max_slots <= 0) d.max_slots = 8;
+        if (d.max_queue <= 0) d.max_queue = 1 << 16;
+        if (d.hbm_budget_bytes == 0) d.hbm_budget_bytes = (size_t)8 << 30;
+    }
+    if (d.max_slots > 64) return set_err(PJAC_EINVAL, "max_slots must be <= 64");
+    auto* sv = new pjac_server();
+    sv->o = d;
+    sv->lanes.resize(d.max_slots);
+    for (auto& L : sv->lanes) {
+        int r = pjac_create(&L.h, &d.solver);
+        cudaError_t e1 = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+        cudaError_t e2 = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+        if (r != PJAC_OK || e1 != cudaSuccess || e2 != cudaSuccess) {
+            pjac_serve_destroy(sv);
+            return r != PJAC_OK ? r : set_err(PJAC_ECUDA, "serve: stream/event creation failed");
+        }
+    }
+    *s = sv;
+    return PJAC_OK;
+}
+
+extern "C" int pjac_serve_destroy(pjac_server* s) {
+    if (!s) return PJAC_OK;
+    for (auto& L : s->lanes) {
+        if (L.st) cudaStreamSynchronize(L.st);
+    }
+    for (auto& L : s->lanes) {
+        if (L.h) pjac_destroy(L.h);
+        if (L.st) cudaStreamDestroy(L.st);
+        if (L.done) cudaEventDestroy(L.done);
+        cudaFree(L.dA); cudaFree(L.dW); cudaFree(L.dV); cudaFree(L.dInfo);
+        cudaFreeHost(L.hA); cudaFreeHost(L.hW); cudaFreeHost(L.hV); cudaFreeHost(L.hInfo);
+    }
+    for (auto& kv : s->all) delete kv.second;
+    delete s;
+    return PJAC_OK;
+}
+
+// Enqueue the work of a lane (its requests are already chosen).
+static int launch_lane(pjac_server* s, Lane& L) {
+    int nb = (int)L.reqs.size();
+    size_t totA = 0, totW = 0;
+    L.ns.resize(nb); L.aoff.resize(nb); L.woff.resize(nb);
+    for (int k = 0; k < nb; ++k) {
+        int n = L.reqs[k]->n;
+        L.ns[k] = n;
+        L.aoff[k] = (int64_t)totA;
+        L.woff[k] = (int64_t)totW;
+        totA += (size_t)n * n;
+        totW += (size_t)n;
+    }
+    int r = PJAC_OK;
+    if ((r = grow_dev(L.dA, L.dA_bytes, totA * 8))) return r;
+    if ((r = grow_dev(L.dV, L.dV_bytes, totA * 8))) return r;
+    if ((r = grow_dev(L.dW, L.dW_bytes, totW * 8))) return r;
+    if ((r = grow_dev(L.dInfo, L.dInfo_bytes, sizeof(pjac_info) * nb))) return r;
+    if ((r = grow_host(L.hA, L.hA_bytes, totA * 8))) return r;
+    if ((r = grow_host(L.hV, L.hV_bytes, totA * 8))) return r;
+    if ((r = grow_host(L.hW, L.hW_bytes, totW * 8))) return r;
+    if ((r = grow_host(L.hInfo, L.hInfo_bytes, sizeof(pjac_info) * nb))) return r;
+    for (int k = 0; k < nb; ++k)
+        memcpy(L.hA + L.aoff[k], L.reqs[k]->a.data(), (size_t)L.ns[k] * L.ns[k] * 8);
+    cudaError_t e = cudaMemcpyAsync(L.dA, L.hA, totA * 8, cudaMemcpyHostToDevice, L.st);
+    if (e != cudaSuccess) return cuda_err(e, "serve H2D");
+    Request* r0 = L.reqs[0];
+    bool batched = r0->n <= BATCH_MAX_N;
+    if (batched) {
+        r = pjac_solve_batched(L.h, nb, L.ns.data(), L.aoff.data(), L.dA, L.woff.data(), L.dW, L.aoff.data(),
+                               L.dV, r0->pivot, r0->tol, L.dInfo, L.st);
+    } else {
+        // single large request: asynchronous single-problem path
+        r = solve_async_dev(L.h, L.dA, r0->n, r0->n, r0->pivot, r0->tol, L.dW, L.dV, r0->n, L.dInfo, L.st);
+    }
+    if (r != PJAC_OK) return r;
+    e = cudaMemcpyAsync(L.hW, L.dW, totW * 8, cudaMemcpyDeviceToHost, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.hV, L.dV, totA * 8, cudaMemcpyDeviceToHost, L.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.hInfo, L.dInfo, sizeof(pjac_info) * nb, cudaMemcpyDeviceToHost, L.st);
+    if (e == cudaSuccess) e = cudaEventRecord(L.done, L.st);
+    if (e != cudaSuccess) return cuda_err(e, "serve D2H");
+    return PJAC_OK;
+}
+
+static void finish_lane(pjac_server* s, Lane& L, int launch_err) {
+    double t = now_ms();
+    for (size_t k = 0; k < L.reqs.size(); ++k) {
+        Request* q = L.reqs[k];
+        if (launch_err != PJAC_OK) {
+            q->status = launch_err;
+            memset(&q->info, 0, sizeof(q->info));
+            q->info.status = launch_err;
+            q->info.n = q->n;
+        } else {
+            int n = q->n;
+            memcpy(q->w_out, L.hW + L.woff[k], (size_t)n * 8);
+            if (q->v_out)
+                for (int c = 0; c < n; ++c)
+                    memcpy(q->v_out + (size_t)c * q->ldv, L.hV + L.aoff[k] + (size_t)c * n, (size_t)n * 8);
+            q->info = L.hInfo[k];
+            q->status = q->info.status;
+        }
+        q->t_done = t;
+        s->lat_ms.push_back(t - q->t_submit);
+        s->last_done = t;
+        s->inflight--;
+        s->in_use -= q->footprint;
+    }
+    L.reqs.clear();
+    L.busy = false;
+}
+
+// One scheduling pass: retire finished lanes, then admit waiting requests.
+static void schedule(pjac_server* s) {
+    for (auto& L : s->lanes) {
+        if (!L.busy) continue;
+        cudaError_t e = cudaEventQuery(L.done);
+        if (e == cudaSuccess) finish_lane(s, L, PJAC_OK);
+        else if (e != cudaErrorNotReady) { cudaGetLastError(); finish_lane(s, L, PJAC_ECUDA); }
+    }
+    for (auto& L : s->lanes) {
+        if (L.busy || s->queue.empty()) continue;
+        Request* head = s->queue.front();
+        if (s->in_use + head->footprint > s->o.hbm_budget_bytes && s->in_use > 0) break;
+        if (head->n > BATCH_MAX_N) {
+            s->queue.pop_front();
+            L.reqs.push_back(head);
+        } else {
+            // micro-batch: every waiting small request with the head's pivot and tol, within budget
+            size_t budget = s->o.hbm_budget_bytes - std::min(s->o.hbm_budget_bytes, s->in_use);
+            size_t used = 0;
+            for (auto it = s->queue.begin(); it != s->queue.end();) {
+                Request* q = *it;
+                if (q->n <= BATCH_MAX_N && q->pivot == head->pivot && q->tol == head->tol &&
+                    (used + q->footprint <= budget || L.reqs.empty()) && L.reqs.size() < 4096) {
+                    used += q->footprint;
+                    L.reqs.push_back(q);
+                    it = s->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (Request* q : L.reqs) {
+            s->in_use += q->footprint;
+            s->inflight++;
+        }
+        s->peak_inflight = std::max(s->peak_inflight, s->inflight);
+        s->peak_hbm = std::max(s->peak_hbm, s->in_use);
+        L.busy = true;
+        int r = launch_lane(s, L);
+        if (r != PJAC_OK) finish_lane(s, L, r);
+    }
+}
+
+extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda, pjac_pivot pivot, double tol,
+                                 double* W, double* V, int ldv, uint64_t* ticket) {
+    if (!s || !A || !W || !ticket) return set_err(PJAC_EINVAL, "NULL argument");
+    if (n < 2 || n > PJAC_MAX_N) return set_err(PJAC_EINVAL, "serve: n = %d outside [2, %d]", n, PJAC_MAX_N);
+    if (lda < n || (V && ldv < n)) return set_err(PJAC_EINVAL, "serve: leading dimension < n");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if ((int)s->queue.size() >= s->o.max_queue) return set_err(PJAC_EAGAIN, "serve: queue full");
+    for (int c = 0; c < n; ++c)
+        for (int r = 0; r < n; ++r) {
+            double v = A[r + (size_t)c * lda];
+            if (!std::isfinite(v) || v != A[c + (size_t)r * lda])
+                return set_err(PJAC_EINVAL, "serve: input has NaN/Inf or is not symmetric");
+        }
+    Request* q = new Request();
+    q->ticket = s->next_ticket++;
+    q->n = n;
+    q->pivot = pivot;
+    q->tol = tol;
+    q->a.resize((size_t)n * n);
+    for (int c = 0; c < n; ++c) memcpy(q->a.data() + (size_t)c * n, A + (size_t)c * lda, (size_t)n * 8);
+    q->w_out = W;
+    q->v_out = V;
+    q->ldv = ldv;
+    q->t_submit = now_ms();
+    q->footprint = request_footprint(n);
+    if (s->first_submit < 0) s->first_submit = q->t_submit;
+    s->queue.push_back(q);
+    s->all[q->ticket] = q;
+    *ticket = q->ticket;
+    schedule(s);
+    return PJAC_OK;
+}
+
+extern "C" int pjac_serve_poll(pjac_server* s, uint64_t ticket, pjac_info* info) {
+    if (!s) return set_err(PJAC_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    schedule(s);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return set_err(PJAC_EINVAL, "serve: unknown or already collected ticket");
+    Request* q = it->second;
+    if (q->status == PJAC_PENDING) return PJAC_PENDING;
+    if (info) *info = q->info;
+    int st = q->status;
+    s->all.erase(it);
+    delete q;
+    return st;
+}
+
+extern "C" int pjac_serve_progress(pjac_server* s) {
+    if (!s) return set_err(PJAC_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    schedule(s);
+    return (int)(s->queue.size() + s->inflight);
+}
+
+extern "C" int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st) {
+    if (!s || !st) return set_err(PJAC_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(st, 0, sizeof(*st));
+    std::vector<double> v = s->lat_ms;
+    st->completed = (int64_t)v.size();
+    st->peak_inflight = s->peak_inflight;
+    st->peak_hbm_bytes = s->peak_hbm;
+    if (v.empty()) return PJAC_OK;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) {
+        double idx = p * (double)(v.size() - 1);
+        size_t lo = (size_t)idx;
+        size_t hi = std::min(v.size() - 1, lo + 1);
+        double f = idx - (double)lo;
+        return v[lo] * (1.0 - f) + v[hi] * f;
+    };
+    st->p50_ms = pct(0.50);
+    st->p99_ms = pct(0.99);
+    st->max_ms = v.back();
+    double sum = 0;
+    for (double x : v) sum += x;
+    st->mean_ms = sum / (double)v.size();
+    double span = (s->last_done - s->first_submit) / 1000.0;
+    st->solves_per_s = span > 0 ? (double)v.size() / span : 0.0;
+    return PJAC_OK;
+}
