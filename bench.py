@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the preconditioned Jacobi eigensolver on B300.
+
+One step = one full solve of the workload through the hot path:
+FP32 diagonalisation -> Newton--Schulz -> A1 = Q^T A Q -> Jacobi (gap rule,
+off-diagonal stop at 1e-15 ||A1||_F) -> readout of W and V, with the input
+resident in HBM.  Workloads (synthetic, seeded; see pjac_inputs):
+  cfg2 (default): n = 1024, 32 clusters of 32 (spread 1e-8)
+  cfg3:           n = 4096, half the spectrum geometric 1..1e-6, half in 64
+                  clusters of 32 (spread 1e-10); --with-4096 adds one timed
+                  cfg3 solve to a cfg2 run
+  batched:        10,000 problems, n log-uniform in [16, 256] (one step = the
+                  whole batch)
+  serve:          Poisson stream at 2000 req/s of n in {64..2048} (one step =
+                  the whole stream; p50/p99 latency reported)
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg3]
+       [--impl reference]
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank solves
+its own copy of the workload (independent problems: replicas, no
+collective); the time is the max over ranks and the value counts all ranks'
+solves.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "eigensolves/s & n=4096 solve time at |dlambda|<=1e-13||A||; gap vs greedy; p99 latency"
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 arithmetic rate of one B300 measured by the FP64 probe
+# (profiles/b300_fp64_probe.md): 476 G DFMA/s -> 0.952 TFLOP/s.
+FP64_PEAK_TFLOPS = 0.952
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the
+    timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if _has_cuda() else "gloo")
+    return ws, rank, local
+
+
+def _has_cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _has_cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def launches_per_solve(n, ns_steps=3):
+    """Kernels of ours launched by one pjac_solve (fixed by the pipeline):
+    input check 1, FP32 diagonaliser 1 (cooperative), FP32->FP64 copy 1,
+    Newton-Schulz 4 per step, transform 2 + symmetrise 1, Jacobi 1,
+    readout 2."""
+    return 1 + 1 + 1 + 4 * ns_steps + 3 + 1 + 2
+
+
+def bench_config(args, n):
+    """The workload description both arms print."""
+    return {"workload": "%s: n=%d, gap rule, off-diagonal stop 1e-15 ||A1||_F, eigenvalues and vectors"
+                        % (args.workload, n),
+            "n": n, "pivot": "gap", "tol": 1e-15,
+            "l2": ("input (%d MB) larger than L2 (126 MB)" % (8 * n * n // 2**20)) if n >= 4096
+            else "input smaller than L2; every step rewrites more than L2 of workspace (A1, V, products)",
+            "parallelism": "replicas (independent problems, no collective)" if args.gpus > 1 else "single GPU"}
+
+
+def workload_problem(name, n=None):
+    import pjac_inputs as pin
+    if name in ("cfg2", "cfg3"):
+        return pin.config_problem(name, n=n)
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ----------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = workload_problem(args.workload, args.n)
+    n = p.n
+    cores = os.cpu_count()
+    values = []
+    samples = []
+    t_pre = None
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        q0 = oracle.q0_fp32(p.a)
+        q, a1 = oracle.precondition(p.a, q0)
+        t1 = time.perf_counter()
+        budget = args.ref_rotations
+        r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=budget)
+        t2 = time.perf_counter()
+        rot_rate = r["rotations"] / max(t2 - t1, 1e-9)
+        # rotations of a full solve: the gap rule needs ~1.8 sweeps of
+        # n(n-1)/2 rotations at this accuracy (measured on the oracle at
+        # n = 300, 520, 1024: 1.94, 1.85, 1.77 sweeps)
+        need = 1.8 * n * (n - 1) / 2
+        t_solve = (t1 - t0) + need / rot_rate
+        if step >= args.warmup:
+            values.append(1.0 / t_solve)
+            samples.append(t_solve)
+        t_pre = t1 - t0
+    v = float(np.median(values))
+    unit = "solves/s"
+    sample = ("oracle preconditioner (LAPACK FP32 eigh + FP64 Newton-Schulz + Q^T A Q on %d threads) in full, "
+              "then %d Jacobi rotations of the gap rule (C, one thread), extrapolated to 1.8 sweeps of "
+              "n(n-1)/2 rotations" % (cores, args.ref_rotations))
+    out = {"metric": METRIC, "value": v, "unit": unit, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": bench_config(args, n),
+           "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+                            "precondition_s": t_pre},
+           "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def cpu_baseline_single(p, rotations_needed, rot_budget):
+    """Time the oracle as it stands on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    q0 = oracle.q0_fp32(p.a)
+    q, a1 = oracle.precondition(p.a, q0)
+    t1 = time.perf_counter()
+    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=rot_budget)
+    t2 = time.perf_counter()
+    rate = r["rotations"] / max(t2 - t1, 1e-9)
+    t_solve = (t1 - t0) + rotations_needed / rate
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": ("preconditioner in full (LAPACK FP32 eigh + Newton-Schulz + Q^T A Q, numpy threads), then "
+                       "%d gap-rule Jacobi rotations of the C oracle (one thread) at %.0f rotations/s, "
+                       "extrapolated to the %d rotations the solve takes (the oracle follows the same pivot "
+                       "sequence as the GPU on the same A1)" % (r["rotations"], rate, rotations_needed)),
+            "precondition_s": t1 - t0, "oracle_rotations_per_s": rate}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2607_23187_b300 import pjac
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workload_problem(args.workload, args.n)
+    n = p.n
+    h = pjac.Handle(transform=args.transform, cluster_size=args.cluster)
+    a = torch.tensor(p.a, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve(pivot="gap", stop="offdiag", tol=1e-15, mat=None):
+        h.set_opts(transform=args.transform, stop=stop, cluster_size=args.cluster)
+        return pjac.pjac_solve(h, a if mat is None else mat, pivot, tol)
+
+    # warm-up (also the accuracy check)
+    info = None
+    for _ in range(args.warmup):
+        w, v, info, st = solve()
+    torch.cuda.synchronize()
+    w_np = w.cpu().numpy()
+    eig_err = float(np.max(np.abs(w_np - p.lam)))
+    v_np = v.cpu().numpy()
+    resid = float(np.linalg.norm(p.a @ v_np - v_np * w_np) / np.linalg.norm(p.a))
+    orth = float(np.linalg.norm(v_np.T @ v_np - np.eye(n)))
+
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        w, v, inf, st = solve()
+        infos.append(inf)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ws, ms_total)
+    ms_step = ms_total / args.steps
+    value = ws * args.steps / (ms_total / 1000.0)
+
+    # end to end through the public API with host buffers
+    a_host = torch.tensor(p.a).pin_memory()
+    w_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    v_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_steps = max(1, min(args.steps, 2))
+    e0.record(stream)
+    for _ in range(e_steps):
+        a_dev = a_host.to(dev, non_blocking=True)
+        h.set_opts(transform=args.transform, cluster_size=args.cluster)
+        w_d, v_d, _, _ = pjac.pjac_solve(h, a_dev, "gap", 1e-15)
+        w_host.copy_(w_d, non_blocking=True)
+        v_host.copy_(v_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1)) / e_steps
+
+    # gap vs greedy, and the eigenvalue-only (Theorem 1) gap solve
+    extras = {}
+    if not args.no_extras:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        wg, vg, inf_g, st_g = solve(pivot="greedy")
+        torch.cuda.synchronize()
+        extras["greedy"] = {"ms": 1000 * (time.perf_counter() - t), "rotations": inf_g["rotations"],
+                            "sweeps": inf_g["sweeps"],
+                            "max_abs_eig_err": float(np.max(np.abs(wg.cpu().numpy() - p.lam)))}
+        norm_f = float(np.linalg.norm(p.a))
+        tol_li = 1e-13 * p.norm2 / norm_f
+        t = time.perf_counter()
+        wl, vl, inf_l, st_l = solve(stop="libound", tol=tol_li)
+        torch.cuda.synchronize()
+        extras["gap_theorem1_stop"] = {
+            "ms": 1000 * (time.perf_counter() - t), "rotations": inf_l["rotations"], "sweeps": inf_l["sweeps"],
+            "tol": tol_li, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1",
+            "max_abs_eig_err": float(np.max(np.abs(wl.cpu().numpy() - p.lam)))}
+        if args.with_4096:
+            p4 = workload_problem("cfg3")
+            a4 = torch.tensor(p4.a, device=dev)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            w4, v4, inf4, st4 = solve(mat=a4)
+            torch.cuda.synchronize()
+            extras["cfg3_n4096_gap"] = {"s": time.perf_counter() - t, "rotations": inf4["rotations"],
+                                        "sweeps": inf4["sweeps"], "phases_ms": {
+                                            "precondition": inf4["ms_precond"], "transform": inf4["ms_transform"],
+                                            "jacobi": inf4["ms_jacobi"]},
+                                        "max_abs_eig_err": float(np.max(np.abs(w4.cpu().numpy() - p4.lam))),
+                                        "norm2": p4.norm2}
+            del a4
+        h.set_opts(transform=args.transform, cluster_size=args.cluster)
+
+    # roofline of the dominant kernel (the Jacobi kernel): FP64 arithmetic
+    inf = infos[-1]
+    rot = inf["rotations"]
+    jac_ms = float(np.median([i["ms_jacobi"] for i in infos]))
+    flops = 14.0 * n * rot     # per rotation: rows (2 mul + 2 fma), V (same), 2 key differences
+    achieved = flops / (jac_ms / 1000.0) / 1e12
+    peaks = measured_peaks()
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "jacobi_single_kernel (one cluster of CTAs, one problem)",
+            "peak_source": "measured FP64 DFMA rate (FP64 probe); MEASURED_PEAKS.json has no FP64 figure",
+            "ns_per_rotation": 1e6 * jac_ms / max(rot, 1),
+            "hbm_gbs_equiv": 80.0 * n * rot / (jac_ms / 1000.0) / 1e9,
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(bench_config(args, n), transform=args.transform),
+           "phases_ms": {"precondition": inf["ms_precond"], "transform": inf["ms_transform"],
+                         "jacobi": inf["ms_jacobi"]},
+           "rotations": rot, "sweeps": inf["sweeps"],
+           "accuracy": {"max_abs_eig_err": eig_err, "norm2": p.norm2, "ok_1e-13": eig_err <= 1e-13 * p.norm2,
+                        "residual": resid, "orthogonality": orth},
+           "extras": extras,
+           "e2e": {"value": ws / (e2e_ms / 1000.0), "unit": "solves/s",
+                   "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n + 8 * n * n},
+           "gpu_launches": launches_per_solve(n) * args.steps,
+           "roofline": roof,
+           "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_single(p, rot, args.ref_rotations)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3"])
+    ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
+    ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
+    ap.add_argument("--with-4096", action="store_true", help="add one timed n=4096 (cfg3) solve")
+    ap.add_argument("--transform", default="fp64", choices=["fp64", "split_bf16"])
+    ap.add_argument("--ref-rotations", type=int, default=100000)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

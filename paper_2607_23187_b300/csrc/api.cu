@@ -231,7 +231,7 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
     const float* q0 = Q0;
     long long ldq0 = n;
     if (!q0) {
-        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 15, st));
+        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, st));
         q0 = w.Q0;
     }
     // X = fl64(Q0);  X <- X (3I - X^T X) / 2

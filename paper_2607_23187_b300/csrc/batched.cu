@@ -31,12 +31,37 @@ __device__ __forceinline__ int take_problem(int* counter, int* sh_next) {
 
 __device__ __forceinline__ void rot32b(float app, float aqq, float apq, float& c, float& s) {
     if (apq == 0.0f) { c = 1.0f; s = 0.0f; return; }
+    // hypotf neither overflows nor underflows, so den >= 2|apq| > 0 even
+    // when d == 0 and apq^2 is below the FP32 range (converged clusters)
     float d = app - aqq;
-    float den = fabsf(d) + sqrtf(d * d + 4.0f * apq * apq);
+    float den = fabsf(d) + hypotf(d, 2.0f * apq);
     float t = 2.0f * fabsf(apq) / den;
     if (d != 0.0f && ((d < 0.0f) != (apq < 0.0f))) t = -t;
     c = rsqrtf(1.0f + t * t);
     s = t * c;
+}
+
+// Z = G_a^T X G_b for one 2x2 block with the products summed in the same
+// pairs for the block and its transpose, so the matrix stays exactly
+// symmetric (see diag32.cu).
+__device__ __forceinline__ void rot2x2_symb(float ca, float sa, float cb, float sb, float x00, float x01,
+                                            float x10, float x11, float& z00, float& z01, float& z10,
+                                            float& z11) {
+    const float ga[2][2] = {{ca, -sa}, {sa, ca}};
+    const float gb[2][2] = {{cb, -sb}, {sb, cb}};
+    const float x[2][2] = {{x00, x01}, {x10, x11}};
+    float z[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            float t00 = __fmul_rn(__fmul_rn(ga[0][u], gb[0][v]), x[0][0]);
+            float t11 = __fmul_rn(__fmul_rn(ga[1][u], gb[1][v]), x[1][1]);
+            float t01 = __fmul_rn(__fmul_rn(ga[0][u], gb[1][v]), x[0][1]);
+            float t10 = __fmul_rn(__fmul_rn(ga[1][u], gb[0][v]), x[1][0]);
+            z[u][v] = __fadd_rn(__fadd_rn(t00, t11), __fadd_rn(t01, t10));
+        }
+    z00 = z[0][0]; z01 = z[0][1]; z10 = z[1][0]; z11 = z[1][1];
 }
 
 // Round-robin tournament (circle method) on N players (N even): in round r
@@ -90,17 +115,22 @@ __global__ void __launch_bounds__(BT) b_diag32_kernel(const BatchDesc* desc, int
                 for (int e = threadIdx.x; e < npairs * npairs; e += BT) {
                     int a = e % npairs, b = e / npairs;
                     int pa = pp[a][0], qa = pp[a][1], pb = pp[b][0], qb = pp[b][1];
-                    if (qa >= n || qb >= n) continue;   // dummy player of odd n
+                    // for odd n the dummy player (index n) is always the second of
+                    // its pair; its row/column does not exist and its rotation is
+                    // the identity, but the real partner is still rotated
+                    const bool ra = qa < n, rb = qb < n;
                     float ca = cs[a][0], sa = cs[a][1], cb = cs[b][0], sb = cs[b][1];
-                    float x00 = A[pa + pb * n], x10 = A[qa + pb * n];
-                    float x01 = A[pa + qb * n], x11 = A[qa + qb * n];
-                    float y00 = ca * x00 + sa * x10, y10 = -sa * x00 + ca * x10;
-                    float y01 = ca * x01 + sa * x11, y11 = -sa * x01 + ca * x11;
-                    float z00 = y00 * cb + y01 * sb, z01 = -y00 * sb + y01 * cb;
-                    float z10 = y10 * cb + y11 * sb, z11 = -y10 * sb + y11 * cb;
+                    float x00 = A[pa + pb * n];
+                    float x10 = ra ? A[qa + pb * n] : 0.0f;
+                    float x01 = rb ? A[pa + qb * n] : 0.0f;
+                    float x11 = (ra && rb) ? A[qa + qb * n] : 0.0f;
+                    float z00, z01, z10, z11;
+                    rot2x2_symb(ca, sa, cb, sb, x00, x01, x10, x11, z00, z01, z10, z11);
                     if (a == b && sa != 0.0f) { z01 = 0.0f; z10 = 0.0f; }
-                    A[pa + pb * n] = z00; A[qa + pb * n] = z10;
-                    A[pa + qb * n] = z01; A[qa + qb * n] = z11;
+                    A[pa + pb * n] = z00;
+                    if (ra) A[qa + pb * n] = z10;
+                    if (rb) A[pa + qb * n] = z01;
+                    if (ra && rb) A[qa + qb * n] = z11;
                 }
                 // Q <- Q G on column pairs
                 for (int e = threadIdx.x; e < n * npairs; e += BT) {
@@ -131,8 +161,8 @@ __global__ void __launch_bounds__(BT) b_diag32_kernel(const BatchDesc* desc, int
                 double o2 = 0, a2 = 0;
                 for (int w = 0; w < BT / 32; ++w) { o2 += red[w][0]; a2 += red[w][1]; }
                 int st = 0;
-                if (a2 == 0.0 || o2 <= 1e-13 * a2) st = 1;
-                else if (prev >= 0.0 && sweep >= 3 && o2 > 0.25 * prev) st = 1;
+                if (a2 == 0.0 || o2 <= 1e-15 * a2) st = 1;
+                else if (prev >= 0.0 && sweep >= 4 && o2 > 0.9 * prev) st = 1;
                 prev = o2;
                 stop = st;
             }
@@ -355,7 +385,7 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     int ctas = std::min(nb, sms * 2);
     size_t smem32 = (size_t)2 * SMEM_N32 * SMEM_N32 * sizeof(float);
     BK(cudaFuncSetAttribute(b_diag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-    b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 30);
+    b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 40);
     BK(cudaGetLastError());
     int ns = opts.ns_steps;
     b_precond_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 1, ns);

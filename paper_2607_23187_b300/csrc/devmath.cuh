@@ -72,21 +72,27 @@ __device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
 // computed with integer and FP32 instructions; only entries whose key lies
 // within KEY_TIE of the best key are evaluated exactly.
 //
-// Gap rule: key = floor(2^20 * log2(L~)) with |log2 L~ - log2 L| <= 2^-16
-// (mantissas truncated to 23 bits: 2^-23 relative each; a handful of FP32
-// roundings; __log2f within 2 ulp of a result of magnitude <= 64; the
-// asymptotic forms below are exact to 2^-118).  KEY_TIE = 2^20 * 2^-10, far
-// above twice that bound, so an entry whose key is more than KEY_TIE below
-// the best key has a strictly smaller FP64 score.  When the best key is in
-// the range where FP64 scores are subnormal (L < 2^-1060) every entry is
+// Gap rule: key = floor(2^20 * log2(L~)) with |log2 L~ - log2 L| <= 2^-17
+// + 2^-21: mantissas truncated to 23 bits (2^-23 relative each), a handful
+// of correctly rounded FP32 operations, and __log2f, whose error is at most
+// 2 ulp of its result (|result| <= 64, so <= 2^-17 absolute); the
+// asymptotic forms below are exact to 2^-118.  The key is therefore within
+// 10 units of 2^20 log2 L, and KEY_GAP_TIE = 64 units keeps a 3x margin over
+// twice that: an entry whose key is more than KEY_GAP_TIE below another's
+// has a strictly smaller FP64 score.  When the best key is below 2^-500,
+// where FP64 scores lose relative accuracy to underflow, every entry is
 // evaluated exactly.
 // Greedy rule: key = high 32 bits of |x| (monotone in |x|); entries with the
 // same key are compared on the full |x|.
 // ---------------------------------------------------------------------------
 constexpr int KEY_NONE = INT_MIN;          // no candidate
 constexpr int KEY_ZERO = INT_MIN + 1;      // x == 0: score exactly 0
-constexpr int KEY_GAP_TIE = 1 << 10;
-constexpr int KEY_SUB = -1060 * (1 << 20); // below: FP64 gap scores may be subnormal
+constexpr int KEY_GAP_TIE = 64;
+// Below 2^-500 every candidate is compared exactly: an unscaled FP64 score
+// 2*q2/den loses accuracy only when q*q underflows, which (with
+// max(|d|,|q|) >= 2^-500, else the operands are rescaled) needs
+// L < 2^-1022/2^-500 = 2^-522.
+constexpr int KEY_SUB = -500 * (1 << 20);
 
 __device__ __forceinline__ float mant23(unsigned long long b) {
     return __int_as_float(0x3f800000u | (unsigned)((b >> 29) & 0x7fffffu));

@@ -12,9 +12,13 @@
 // previous buffer through sigma and writes the rotated result to the other
 // buffer, so every access stays within a few elements of a straight stream.
 // The column order of Q0 is irrelevant to the preconditioner.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pjac {
 
@@ -29,24 +33,49 @@ __device__ __forceinline__ int tour_sigma(int p, int m) {
 
 __device__ __forceinline__ void rot32(float app, float aqq, float apq, float& c, float& s) {
     if (apq == 0.0f) { c = 1.0f; s = 0.0f; return; }
+    // hypotf neither overflows nor underflows, so den >= 2|apq| > 0 even
+    // when d == 0 and apq^2 is below the FP32 range (converged clusters)
     float d = app - aqq;
-    float den = fabsf(d) + sqrtf(d * d + 4.0f * apq * apq);
+    float den = fabsf(d) + hypotf(d, 2.0f * apq);
     float t = 2.0f * fabsf(apq) / den;
     if (d != 0.0f && ((d < 0.0f) != (apq < 0.0f))) t = -t;
     c = rsqrtf(1.0f + t * t);
     s = t * c;
 }
 
-// One round.  Blocks [0, T*T) rotate the 32x32 tiles of A; blocks
-// [T*T, 2*T*T) rotate the tiles of Q.  (T = npad/32.)
-__global__ void __launch_bounds__(256) round_kernel(const float* __restrict__ A0, float* __restrict__ A1,
-                                                    const float* __restrict__ Q0, float* __restrict__ Q1,
-                                                    int npad, int n, const int* __restrict__ done) {
-    __shared__ float cs_r[16][2], cs_c[16][2];
-    if (*done) return;
+// Z = G_a^T X G_b (G = [[c,-s],[s,c]]) for one 2x2 block, written as
+// Z[u][v] = (t(0,0) + t(1,1)) + (t(0,1) + t(1,0)) with
+// t(r,w) = (G_a[r][u] * G_b[w][v]) * X[r][w].  The block (b,a) computes the
+// transpose from the same products summed in the same pairs, so the FP32
+// matrix stays exactly symmetric through every round.
+__device__ __forceinline__ void rot2x2_sym(float ca, float sa, float cb, float sb, float x00, float x01,
+                                           float x10, float x11, float& z00, float& z01, float& z10,
+                                           float& z11) {
+    // G[r][u]: G[0][0]=c, G[0][1]=-s, G[1][0]=s, G[1][1]=c
+    const float ga[2][2] = {{ca, -sa}, {sa, ca}};
+    const float gb[2][2] = {{cb, -sb}, {sb, cb}};
+    const float x[2][2] = {{x00, x01}, {x10, x11}};
+    float z[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            float t00 = __fmul_rn(__fmul_rn(ga[0][u], gb[0][v]), x[0][0]);
+            float t11 = __fmul_rn(__fmul_rn(ga[1][u], gb[1][v]), x[1][1]);
+            float t01 = __fmul_rn(__fmul_rn(ga[0][u], gb[1][v]), x[0][1]);
+            float t10 = __fmul_rn(__fmul_rn(ga[1][u], gb[0][v]), x[1][0]);
+            z[u][v] = __fadd_rn(__fadd_rn(t00, t11), __fadd_rn(t01, t10));
+        }
+    z00 = z[0][0]; z01 = z[0][1]; z10 = z[1][0]; z11 = z[1][1];
+}
+
+// One tile of one round.  Tiles [0, T*T) rotate the 32x32 tiles of A; tiles
+// [T*T, 2*T*T) rotate the tiles of Q.  (T = npad/32.)  256 threads.
+__device__ __forceinline__ void round_tile(int b, const float* __restrict__ A0, float* __restrict__ A1,
+                                           const float* __restrict__ Q0, float* __restrict__ Q1, int npad,
+                                           float (*cs_r)[2], float (*cs_c)[2]) {
     const int T = npad / 32;
     const int m = npad / 2;
-    int b = blockIdx.x;
     bool isA = b < T * T;
     if (!isA) b -= T * T;
     const int tr = b % T, tc = b / T;     // tile row (positions tr*32..), tile col
@@ -75,11 +104,8 @@ __global__ void __launch_bounds__(256) round_kernel(const float* __restrict__ A0
         int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
         float x00 = A0[r0 + (long long)c0 * npad], x10 = A0[r1 + (long long)c0 * npad];
         float x01 = A0[r0 + (long long)c1 * npad], x11 = A0[r1 + (long long)c1 * npad];
-        // Y = G_a^T X G_b with G = [[c,-s],[s,c]]
-        float y00 = ca * x00 + sa * x10, y10 = -sa * x00 + ca * x10;
-        float y01 = ca * x01 + sa * x11, y11 = -sa * x01 + ca * x11;
-        float z00 = y00 * cb + y01 * sb, z01 = -y00 * sb + y01 * cb;
-        float z10 = y10 * cb + y11 * sb, z11 = -y10 * sb + y11 * cb;
+        float z00, z01, z10, z11;
+        rot2x2_sym(ca, sa, cb, sb, x00, x01, x10, x11, z00, z01, z10, z11);
         if (rp == cp && sa != 0.0f) { z01 = 0.0f; z10 = 0.0f; }
         A1[rp + (long long)cp * npad] = z00;
         A1[rp + 1 + (long long)cp * npad] = z10;
@@ -94,51 +120,84 @@ __global__ void __launch_bounds__(256) round_kernel(const float* __restrict__ A0
             Q1[r + (long long)(cp + 1) * npad] = -q0 * sb + q1 * cb;
         }
     }
+    __syncthreads();
 }
 
-__global__ void init32_kernel(const double* A, long long lda, int n, int npad, float* A32, float* Q32) {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long tot = (long long)npad * npad;
-    for (; e < tot; e += (long long)gridDim.x * blockDim.x) {
+// The whole diagonalisation in one cooperative launch: rounds separated by
+// grid-wide barriers, the convergence test after every sweep decided by
+// every CTA from the same global sums.  acc: 4 doubles, zero on entry.
+__global__ void __launch_bounds__(256) diag32_coop_kernel(const double* __restrict__ A, long long lda, int n,
+                                                          int npad, float* Ab0, float* Ab1, float* Qb0,
+                                                          float* Qb1, float* Qout, double* acc,
+                                                          int max_sweeps) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ float cs_r[16][2], cs_c[16][2];
+    __shared__ double s_off[8], s_all[8];
+    const long long nn = (long long)npad * npad;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gstride) {
         int r = (int)(e % npad), c = (int)(e / npad);
-        A32[e] = (r < n && c < n) ? (float)A[r + (long long)c * lda] : 0.0f;
-        Q32[e] = (r == c) ? 1.0f : 0.0f;
+        Ab0[e] = (r < n && c < n) ? (float)A[r + (long long)c * lda] : 0.0f;
+        Qb0[e] = (r == c) ? 1.0f : 0.0f;
     }
-}
-
-// Convergence test after a sweep (device side, no host round trip).
-// st: [0] done flag, [1] index of the buffer holding the result, [2] sweeps;
-// acc: off^2, ||A||^2 of this sweep, then the previous sweep's off^2.
-__global__ void conv32_kernel(double* acc, int* st, int cur) {
-    if (st[0]) return;
-    double o2 = acc[0], a2 = acc[1], prev = acc[2];
-    int sweep = st[2];
-    st[1] = cur;
-    st[2] = sweep + 1;
-    bool stop = (a2 == 0.0 || o2 <= 1e-13 * a2) || (sweep >= 3 && prev >= 0.0 && o2 > 0.25 * prev);
-    acc[2] = o2;
-    acc[0] = 0.0;
-    acc[1] = 0.0;
-    if (stop) st[0] = 1;
-}
-
-__global__ void conv32_init_kernel(double* acc, int* st) {
-    acc[0] = 0.0; acc[1] = 0.0; acc[2] = -1.0;
-    st[0] = 0; st[1] = 0; st[2] = 0;
-}
-
-__global__ void extract_q_kernel(const float* QA, const float* QB, const int* st, int npad, int n, float* Q0) {
-    const float* Q32 = st[1] ? QB : QA;
+    grid.sync();
+    float* Ab[2] = {Ab0, Ab1};
+    float* Qb[2] = {Qb0, Qb1};
+    const int T = npad / 32;
+    const int ntiles = 2 * T * T;
+    int cur = 0;
+    double prev = -1.0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int r = 0; r < npad - 1; ++r) {
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+                round_tile(t, Ab[cur], Ab[cur ^ 1], Qb[cur], Qb[cur ^ 1], npad, cs_r, cs_c);
+            cur ^= 1;
+            grid.sync();
+        }
+        // off(A)^2 and ||A||^2 of the FP32 matrix, in slot (sweep & 1)
+        double off = 0.0, all = 0.0;
+        const float* Ac = Ab[cur];
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += gstride) {
+            int rr = (int)(e % npad), cc = (int)(e / npad);
+            double v = (double)Ac[e];
+            all += v * v;
+            if (rr != cc) off += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_off[threadIdx.x >> 5] = off; s_all[threadIdx.x >> 5] = all; }
+        __syncthreads();
+        double* slot = acc + 2 * (sweep & 1);
+        if (threadIdx.x == 0) {
+            double o2 = 0, a2 = 0;
+            for (int w = 0; w < 8; ++w) { o2 += s_off[w]; a2 += s_all[w]; }
+            atomicAdd(slot, o2);
+            atomicAdd(slot + 1, a2);
+        }
+        grid.sync();
+        double o2 = __ldcg(slot), a2 = __ldcg(slot + 1);
+        bool stop = (a2 == 0.0 || o2 <= 1e-15 * a2) || (sweep >= 4 && prev >= 0.0 && o2 > 0.9 * prev);
+        prev = o2;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double* other = acc + 2 * ((sweep + 1) & 1);
+            other[0] = 0.0;
+            other[1] = 0.0;
+        }
+        if (stop) break;
+        grid.sync();   // the other slot is zero before anyone adds to it
+    }
     // Q0 (n x n, ld n).  After whole sweeps (npad-1 rounds each) every
     // player is back at its own position, so the first n positions are the
     // real indices; padding indices are zero rows/columns that only ever
     // take identity rotations, so their columns of Q are unit vectors of
     // padding rows and are dropped.
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long tot = (long long)n * n;
-    for (; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const float* Qc = Qb[cur];
+    const long long tot = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gstride) {
         int r = (int)(e % n), c = (int)(e / n);
-        Q0[e] = Q32[r + (long long)c * npad];
+        Qout[e] = Qc[r + (long long)c * npad];
     }
 }
 
@@ -147,64 +206,30 @@ size_t diag_fp32_ws_floats(int n) {
     return (size_t)(4 * npad * npad + 64);
 }
 
-
-// off^2 / ||A||^2 of the current buffer, skipped once converged.
-__global__ void off32_gated_kernel(const float* A, int npad, double* acc, const int* done) {
-    if (*done) return;
-    __shared__ double s_off[8], s_all[8];
-    double off = 0.0, all = 0.0;
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long tot = (long long)npad * npad;
-    for (; e < tot; e += (long long)gridDim.x * blockDim.x) {
-        int r = (int)(e % npad), c = (int)(e / npad);
-        double v = (double)A[e];
-        all += v * v;
-        if (r != c) off += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        all += __shfl_xor_sync(0xffffffffu, all, o);
-    }
-    if ((threadIdx.x & 31) == 0) { s_off[threadIdx.x >> 5] = off; s_all[threadIdx.x >> 5] = all; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int w = 0; w < 8; ++w) { a += s_off[w]; b += s_all[w]; }
-        atomicAdd(acc, a);
-        atomicAdd(acc + 1, b);
-    }
-}
-
 // Q0 <- eigenvectors of fl32(A) (approximately).  ws: diag_fp32_ws_floats(n)
-// floats.  Entirely asynchronous: after every sweep a device-side test sets
-// a flag that turns the remaining launches into no-ops.
+// floats.  One cooperative launch; nothing waits on the host.
 cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
                       int max_sweeps, cudaStream_t st) {
     (void)iws;
     int npad = ((n + 31) / 32) * 32;
     long long nn = (long long)npad * npad;
-    float* Ab[2] = {ws, ws + nn};
-    float* Qb[2] = {ws + 2 * nn, ws + 3 * nn};
-    double* acc = reinterpret_cast<double*>(ws + 4 * nn);   // 3 doubles (8-byte aligned: nn even)
-    int* flags = reinterpret_cast<int*>(acc + 4);           // 3 ints
-    init32_kernel<<<592, 256, 0, st>>>(A, lda, n, npad, Ab[0], Qb[0]);
-    conv32_init_kernel<<<1, 1, 0, st>>>(acc, flags);
-    cudaError_t e = cudaGetLastError();
+    float* Ab0 = ws;
+    float* Ab1 = ws + nn;
+    float* Qb0 = ws + 2 * nn;
+    float* Qb1 = ws + 3 * nn;
+    double* acc = reinterpret_cast<double*>(ws + 4 * nn);   // 8-byte aligned: nn is even
+    cudaError_t e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), st);
     if (e != cudaSuccess) return e;
-    int cur = 0;
-    const int T = npad / 32;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        for (int r = 0; r < npad - 1; ++r) {
-            round_kernel<<<2 * T * T, 256, 0, st>>>(Ab[cur], Ab[cur ^ 1], Qb[cur], Qb[cur ^ 1], npad, n, flags);
-            cur ^= 1;
-        }
-        off32_gated_kernel<<<296, 256, 0, st>>>(Ab[cur], npad, acc, flags);
-        conv32_kernel<<<1, 1, 0, st>>>(acc, flags, cur);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    extract_q_kernel<<<592, 256, 0, st>>>(Qb[0], Qb[1], flags, npad, n, Q0);
-    return cudaGetLastError();
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, diag32_coop_kernel, 256, 0);
+    if (e != cudaSuccess) return e;
+    int T = npad / 32;
+    int grid = std::min(sms * std::max(1, std::min(per_sm, 4)), 2 * T * T);
+    void* args[] = {(void*)&A, (void*)&lda, (void*)&n, (void*)&npad, (void*)&Ab0, (void*)&Ab1, (void*)&Qb0,
+                    (void*)&Qb1, (void*)&Q0, (void*)&acc, (void*)&max_sweeps};
+    return cudaLaunchCooperativeKernel((const void*)diag32_coop_kernel, dim3(grid), dim3(256), args, 0, st);
 }
 
 }  // namespace pjac

@@ -46,17 +46,30 @@ struct Slot {
 };
 
 struct Sh {
+    int wk3[NT / 32][3];
+    int wn3[NT / 32][3];
+    Cand out3[3];
     int wkey[NT / 32];
     Cand wc[NT / 32];
     double wsum[NT / 32];
     Cand out;
     Slot slots[2];
+    Slot inbox[2][16];      // slot of every cluster rank, pushed by the sender
     Cand sel;
+    int tflag, pad3;
     double c, s, t, dii, djj, q;
     double normf, thr, eps_li, scale;
     int pi, pj, nresc, decision;
     int key_eps, pad2;
 };
+
+#ifdef PJAC_PROFILE
+// Profiling build only: per-phase clock totals of CTA 0 and event counts.
+__device__ unsigned long long g_prof[16];
+#define PROF_ADD(k, v) atomicAdd(&g_prof[k], (unsigned long long)(v))
+#else
+#define PROF_ADD(k, v) ((void)0)
+#endif
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double* p, double v) { __stcg(p, v); }
@@ -74,7 +87,10 @@ __device__ __forceinline__ int entry_key(int pivot, double x, double dd) {
 // Exact score of a candidate (gap: Eq. (1.1) in FP64; greedy: |x|).
 __device__ __forceinline__ double cand_value(Cand& c, int pivot, const double* diag) {
     if (pivot == PJAC_PIVOT_GREEDY) return fabs(c.x);
-    if (c.ex < 0.0) c.ex = gap_exact(diag[c.row], diag[c.col], c.x);
+    if (c.ex < 0.0) {
+        c.ex = gap_exact(diag[c.row], diag[c.col], c.x);
+        PROF_ADD(8, 1);
+    }
     return c.ex;
 }
 
@@ -88,6 +104,9 @@ __device__ __forceinline__ bool exact_better(double va, const Cand& a, double vb
 __device__ __forceinline__ bool better(Cand& a, Cand& b, int pivot, const double* diag) {
     if (a.key == KEY_NONE) return false;
     if (b.key == KEY_NONE) return true;
+    // the same unordered pair seen from its two rows: equal scores
+    if (a.row == b.col && a.col == b.row) return a.row < b.row;
+    if (a.row == b.row && a.col == b.col) return false;
     if (pivot == PJAC_PIVOT_GREEDY) {
         if (a.key != b.key) return a.key > b.key;
     } else {
@@ -179,6 +198,118 @@ __device__ Cand block_select(Cand mine, int pivot, const double* diag, Sh& sh) {
     return r;
 }
 
+// Phase 2 of a block selection: exact argmax among the contenders (uniform
+// call, used when several threads are within the tie band).
+__device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag, Sh& sh) {
+    double v = -2.0;
+    if (cont) v = cand_value(mine, pivot, diag);
+    int lane = threadIdx.x & 31;
+    double bv = v;
+    int br = mine.row, bc = mine.col, bl = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        int orr = __shfl_xor_sync(0xffffffffu, br, off);
+        int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        bool take = (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
+        if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
+    }
+    if (lane == bl) {
+        Cand w = mine;
+        if (bv < -1.0) w.key = KEY_NONE;
+        sh.wc[threadIdx.x >> 5] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Cand best = no_cand();
+        double vb = -2.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            Cand c = sh.wc[w];
+            if (c.key == KEY_NONE) continue;
+            double vc = cand_value(c, pivot, diag);
+            if (best.key == KEY_NONE || exact_better(vc, c, vb, best)) { best = c; vb = vc; }
+        }
+        sh.out = best;
+    }
+    __syncthreads();
+    Cand r = sh.out;
+    __syncthreads();
+    return r;
+}
+
+// Three independent block-wide exact argmaxes (one candidate of each kind
+// per thread) in one pass: one barrier for the three maximum keys, one for
+// the contender counts, one for the results; the exact phase runs only for
+// a kind with several contenders.  Uniform call.
+__device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tie = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_GAP_TIE;
+    int w0 = __reduce_max_sync(0xffffffffu, c0.key);
+    int w1 = __reduce_max_sync(0xffffffffu, c1.key);
+    int w2 = __reduce_max_sync(0xffffffffu, c2.key);
+    if (lane == 0) { sh.wk3[warp][0] = w0; sh.wk3[warp][1] = w1; sh.wk3[warp][2] = w2; }
+    __syncthreads();
+    int m[3] = {sh.wk3[0][0], sh.wk3[0][1], sh.wk3[0][2]};
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+        m[0] = max(m[0], sh.wk3[w][0]);
+        m[1] = max(m[1], sh.wk3[w][1]);
+        m[2] = max(m[2], sh.wk3[w][2]);
+    }
+    Cand cs[3] = {c0, c1, c2};
+    bool t[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        bool exact_all = (pivot != PJAC_PIVOT_GREEDY) && m[q] < KEY_SUB;
+        t[q] = m[q] != KEY_NONE && cs[q].key != KEY_NONE &&
+               (exact_all || (long long)cs[q].key >= (long long)m[q] - tie);
+        unsigned b = __ballot_sync(0xffffffffu, t[q]);
+        if (lane == 0) sh.wn3[warp][q] = __popc(b);
+    }
+    __syncthreads();
+    int cnt[3] = {0, 0, 0};
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        cnt[0] += sh.wn3[w][0];
+        cnt[1] += sh.wn3[w][1];
+        cnt[2] += sh.wn3[w][2];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (cnt[q] == 1 && t[q]) sh.out3[q] = cs[q];
+    __syncthreads();
+    Cand r[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        r[q] = (cnt[q] == 1) ? sh.out3[q] : no_cand();
+        if (cnt[q] > 1) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh);
+    }
+    c0 = r[0];
+    c1 = r[1];
+    c2 = r[2];
+}
+
+// Best candidate over the first `width` lanes of a warp (width a power of
+// two <= 32; butterfly, every lane of the group ends with the maximum).  The
+// row and column travel packed in one word; a received candidate's exact
+// score is recomputed if a comparison needs it.
+__device__ __forceinline__ Cand warp_best(Cand c, int width, int pivot, const double* diag) {
+    for (int off = width >> 1; off > 0; off >>= 1) {
+        Cand o;
+        o.key = __shfl_xor_sync(0xffffffffu, c.key, off);
+        int rc = __shfl_xor_sync(0xffffffffu, (c.row << 16) | (c.col & 0xffff), off);
+        o.row = rc >> 16;
+        o.col = rc & 0xffff;
+        o.pad = 0;
+        o.x = __shfl_xor_sync(0xffffffffu, c.x, off);
+        o.ex = -1.0;
+        if (o.key == KEY_NONE) { o.row = -1; o.col = -1; }
+        if (better(o, c, pivot, diag)) c = o;
+    }
+    return c;
+}
+
 __device__ __forceinline__ double block_sum(double v, Sh& sh) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -230,10 +361,12 @@ __device__ __forceinline__ const Slot* peer_slot(Sh& sh, int par, int r) {
 }
 
 // Rescan row k (block-wide): best entry over l != k.
-__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh) {
+// Rescan row k (block-wide): its best entry over l != k, and in sec the
+// best entry in any other column (the top two of the row).
+__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& sec) {
     const double* row = a.A + (long long)k * a.lda;
     double dk = diag[k];
-    Cand best = no_cand();
+    Cand t1 = no_cand(), t2 = no_cand();
     for (int l0 = threadIdx.x; l0 < a.n; l0 += 4 * NT) {
         double xs[4];
 #pragma unroll
@@ -248,10 +381,14 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh) 
             Cand c;
             c.row = k; c.col = l; c.pad = 0; c.x = xs[u]; c.ex = -1.0;
             c.key = entry_key(a.pivot, xs[u], a.pivot == PJAC_PIVOT_GREEDY ? 0.0 : __dadd_rn(dk, -diag[l]));
-            if (better(c, best, a.pivot, diag)) best = c;
+            if (better(c, t1, a.pivot, diag)) { t2 = t1; t1 = c; }
+            else if (better(c, t2, a.pivot, diag)) t2 = c;
         }
     }
-    return block_select(best, a.pivot, diag, sh);
+    Cand b = block_select(t1, a.pivot, diag, sh);
+    Cand offer = (t1.key != KEY_NONE && t1.col == b.col) ? t2 : t1;
+    sec = block_select(offer, a.pivot, diag, sh);
+    return b;
 }
 
 // off(A)^2 * 2^-2e over the owned rows, e = ilogb(||A1||_F) (as the oracle).
@@ -269,10 +406,12 @@ __device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, S
 }
 
 // Solve one problem.  rank/P: this CTA's rank in the cluster and the
-// cluster size.  Shared arrays: diag[n], cache[m], resc[m].
+// cluster size.  Shared arrays: diag[n], cache[m] (best entry of each owned
+// row), cache2[m] (best entry in another column, or none when unknown),
+// resc[m].
 template <bool CLUSTER>
 __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double* diag,
-                               Cand* cache, int* resc) {
+                               Cand* cache, Cand* cache2, int* resc) {
     const int n = a.n;
     const int tid = threadIdx.x;
     const int mchunk = (n + P - 1) / P;
@@ -280,6 +419,12 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     const int k1 = min(n, k0 + mchunk);
     const int pivot = a.pivot;
     long long start = clock64();
+#ifdef PJAC_PROFILE
+    long long pt = clock64();
+#define LAP(k) do { if (rank == 0 && tid == 0) { long long nw = clock64(); PROF_ADD(k, nw - pt); pt = nw; } } while (0)
+#else
+#define LAP(k) ((void)0)
+#endif
 
     for (int k = tid; k < n; k += NT) diag[k] = ldcg(a.A + (long long)k * a.lda + k);
 
@@ -355,6 +500,27 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     };
 
     // ---- rotate rows/cols i,j for the owned indices, and V ----
+    // Loads of the entries a rotation (i,j) changes, issued before the
+    // rotation parameters are known (they depend only on i, j).
+    double px[MAXR], py[MAXR], pvx[MAXR], pvy[MAXR];
+    auto preload = [&](int i, int j) {
+        const double* Ai = a.A + (long long)i * a.lda;
+        const double* Aj = a.A + (long long)j * a.lda;
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            int k = k0 + tid + r * NT;
+            px[r] = py[r] = pvx[r] = pvy[r] = 0.0;
+            if (k < k1) {
+                px[r] = ldcg(Ai + k);
+                py[r] = ldcg(Aj + k);
+                if (a.V) {
+                    pvx[r] = a.V[(long long)i * a.ldv + k];
+                    pvy[r] = a.V[(long long)j * a.ldv + k];
+                }
+            }
+        }
+    };
+
     auto rotate_owned = [&](int i, int j, const double c, const double s, const double dii_new,
                             const double djj_new, bool score, Cand& pI, Cand& pJ) {
         double* Ai = a.A + (long long)i * a.lda;
@@ -368,7 +534,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             if (a.V) {
                 double* Vi = a.V + (long long)i * a.ldv;
                 double* Vj = a.V + (long long)j * a.ldv;
-                double vx = Vi[k], vy = Vj[k];
+                double vx = pvx[r], vy = pvy[r];
                 Vi[k] = __fma_rn(c, vx, __dmul_rn(s, vy));
                 Vj[k] = __fma_rn(c, vy, -__dmul_rn(s, vx));
             }
@@ -394,7 +560,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 }
                 continue;
             }
-            double x = ldcg(Ai + k), y = ldcg(Aj + k);
+            double x = px[r], y = py[r];
             double xn = __fma_rn(c, x, __dmul_rn(s, y));
             double yn = __fma_rn(c, y, -__dmul_rn(s, x));
             double* Ak = a.A + (long long)k * a.lda;
@@ -416,21 +582,59 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             Cand cj; cj.key = ky; cj.row = j; cj.col = k; cj.pad = 0; cj.x = yn; cj.ex = -1.0;
             if (better(ci, pI, pivot, diag)) pI = ci;
             if (better(cj, pJ, pivot, diag)) pJ = cj;
-            // own row k: compare with its cached best, or rescan
+            // own row k: only its entries (k,i), (k,j) changed.  Keep its best
+            // entry and, when known, its best entry in another column;
+            // rescan only when neither survives.
+            Cand e1, e2;
+            e1.row = k; e1.pad = 0; e1.ex = -1.0;
+            e2 = e1;
+            if (cmin == i) { e1.col = i; e1.key = kx; e1.x = xn; e2.col = j; e2.key = ky; e2.x = yn; }
+            else           { e1.col = j; e1.key = ky; e1.x = yn; e2.col = i; e2.key = kx; e2.x = xn; }
+            (void)cmax;
             Cand cur = cache[k - k0];
+            Cand sec = cache2[k - k0];
+            if (sec.key != KEY_NONE && (sec.col == i || sec.col == j)) sec = no_cand();
             if (cur.col == i || cur.col == j) {
-                int slot = atomicAdd(&sh.nresc, 1);
-                resc[slot] = k;
+                if (sec.key == KEY_NONE) {
+                    int slot = atomicAdd(&sh.nresc, 1);
+                    resc[slot] = k;
+                } else {
+                    // every untouched entry is <= sec
+                    Cand nb = sec;
+                    int w = 0;
+                    if (better(e1, nb, pivot, diag)) { nb = e1; w = 1; }
+                    if (better(e2, nb, pivot, diag)) { nb = e2; w = 2; }
+                    if (w == 0) {
+                        cur = sec;
+                        sec = no_cand();
+                    } else {
+                        Cand other = (w == 1) ? e2 : e1;
+                        cur = nb;
+                        if (better(other, sec, pivot, diag)) sec = other;
+                    }
+                    cache[k - k0] = cur;
+                    cache2[k - k0] = sec;
+                }
             } else {
-                Cand e1, e2;
-                e1.row = k; e1.pad = 0; e1.ex = -1.0;
-                e2 = e1;
-                if (cmin == i) { e1.col = i; e1.key = kx; e1.x = xn; e2.col = j; e2.key = ky; e2.x = yn; }
-                else           { e1.col = j; e1.key = ky; e1.x = yn; e2.col = i; e2.key = kx; e2.x = xn; }
-                (void)cmax;
-                if (better(e1, cur, pivot, diag)) cur = e1;
-                if (better(e2, cur, pivot, diag)) cur = e2;
+                Cand nb = cur;
+                int w = 0;
+                if (better(e1, nb, pivot, diag)) { nb = e1; w = 1; }
+                if (better(e2, nb, pivot, diag)) { nb = e2; w = 2; }
+                if (w == 0) {
+                    if (sec.key != KEY_NONE) {
+                        if (better(e1, sec, pivot, diag)) sec = e1;
+                        if (better(e2, sec, pivot, diag)) sec = e2;
+                    }
+                } else {
+                    // the old best bounds every untouched entry
+                    Cand other = (w == 1) ? e2 : e1;
+                    Cand ns = cur;
+                    if (better(other, ns, pivot, diag)) ns = other;
+                    cur = nb;
+                    sec = ns;
+                }
                 cache[k - k0] = cur;
+                cache2[k - k0] = sec;
             }
         }
     };
@@ -460,6 +664,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     if (tid == 0) { diag[i] = dii; diag[j] = djj; }
                     __syncthreads();
                     Cand d1 = no_cand(), d2 = no_cand();
+                    preload(i, j);
                     rotate_owned(i, j, c, s, dii, djj, false, d1, d2);
                     rot++;
                     any = true;
@@ -473,8 +678,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     } else {
         // initial scan (Sec. 3.2: O(n^2) scores once)
         for (int k = k0; k < k1; ++k) {
-            Cand b = rescan_row(a, k, diag, sh);
-            if (tid == 0) cache[k - k0] = b;
+            Cand s2;
+            Cand b = rescan_row(a, k, diag, sh, s2);
+            if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; }
         }
         __syncthreads();
         // first selection
@@ -507,9 +713,15 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         }
         bool stop_now = false;
         for (;;) {
+            LAP(7);
             if (rot % ce == 0) {
                 offdiag_check(stop_now);
                 if (stop_now) break;
+            }
+            LAP(0);
+            {
+                Cand g0 = sh.sel;
+                if (g0.key != KEY_NONE) preload(min(g0.row, g0.col), max(g0.row, g0.col));
             }
             // decisions on the current selection (thread 0, then broadcast)
             if (tid == 0) {
@@ -548,6 +760,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 sh.nresc = 0;
             }
             __syncthreads();
+            LAP(1);
             if (sh.decision == 1) { status = PJAC_OK; break; }
             if (sh.decision == 3) { status = PJAC_ENOCONV; break; }
             const int i = sh.pi, j = sh.pj;
@@ -556,14 +769,20 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             rotate_owned(i, j, c, s, dii, djj, true, pI, pJ);
             rot++;
             __syncthreads();
+            LAP(2);
             // rescans of owned rows whose best was in column i or j
             const int nr = sh.nresc;
+            if (tid == 0) PROF_ADD(9, nr);
             for (int r = 0; r < nr; ++r) {
                 int k = resc[r];
-                Cand b = rescan_row(a, k, diag, sh);
-                if (tid == 0) cache[k - k0] = b;
+                Cand s2;
+                Cand b = rescan_row(a, k, diag, sh, s2);
+                if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; }
             }
             __syncthreads();
+            LAP(3);
+            if (tid == 0)
+                sh.tflag = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
             Cand loc = no_cand();
 #pragma unroll
             for (int r = 0; r < MAXR; ++r) {
@@ -573,39 +792,54 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 Cand cc = cache[k - k0];
                 if (better(cc, loc, pivot, diag)) loc = cc;
             }
-            loc = block_select(loc, pivot, diag, sh);
-            pI = block_select(pI, pivot, diag, sh);
-            pJ = block_select(pJ, pivot, diag, sh);
-            if (tid == 0) {
-                sh.slots[par].loc = loc;
-                sh.slots[par].pi = pI;
-                sh.slots[par].pj = pJ;
-                sh.slots[par].flags = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
+            block_select3(loc, pI, pJ, pivot, diag, sh);
+            LAP(4);
+            // push this CTA's slot into every rank's inbox (remote stores
+            // before the barrier), then reduce locally after it
+            if (tid < P) {
+                Slot my;
+                my.loc = loc; my.pi = pI; my.pj = pJ; my.sum = 0.0; my.flags = sh.tflag; my.pad = 0;
+                if (CLUSTER) {
+                    cg::cluster_group cl = cg::this_cluster();
+                    *cl.map_shared_rank(&sh.inbox[par][rank], tid) = my;
+                } else {
+                    sh.inbox[par][0] = my;
+                }
             }
             cta_exchange_sync<CLUSTER>();
-            if (tid == 0) {
-                Cand bi = no_cand(), bj = no_cand(), g = no_cand();
-                for (int r = 0; r < P; ++r) {
-                    const Slot* ps = peer_slot<CLUSTER>(sh, par, r);
-                    Cand ci = ps->pi, cj = ps->pj;
-                    if (better(ci, bi, pivot, diag)) bi = ci;
-                    if (better(cj, bj, pivot, diag)) bj = cj;
+            LAP(5);
+            // three warps reduce the three kinds of candidates in parallel
+            {
+                const int warp = tid >> 5, lane = tid & 31;
+                int width = 1;
+                while (width < P) width <<= 1;
+                if (warp < 3) {
+                    Cand c = no_cand();
+                    if (lane < P) {
+                        const Slot& sl = sh.inbox[par][lane];
+                        c = (warp == 0) ? sl.loc : (warp == 1 ? sl.pi : sl.pj);
+                    }
+                    c = warp_best(c, width, pivot, diag);
+                    if (lane == 0) sh.out3[warp] = c;
                 }
-                for (int r = 0; r < P; ++r) {
-                    Cand cl = peer_slot<CLUSTER>(sh, par, r)->loc;
-                    if (better(cl, g, pivot, diag)) g = cl;
+                __syncthreads();
+                if (tid == 0) {
+                    Cand g = sh.out3[0], bi = sh.out3[1], bj = sh.out3[2];
+                    if (better(bi, g, pivot, diag)) g = bi;
+                    if (better(bj, g, pivot, diag)) g = bj;
+                    if (i >= k0 && i < k1) { cache[i - k0] = bi; cache2[i - k0] = no_cand(); }
+                    if (j >= k0 && j < k1) { cache[j - k0] = bj; cache2[j - k0] = no_cand(); }
+                    sh.sel = g;
+                    sh.decision = (sh.inbox[par][0].flags & 1) ? 2 : 0;
                 }
-                if (better(bi, g, pivot, diag)) g = bi;
-                if (better(bj, g, pivot, diag)) g = bj;
-                if (i >= k0 && i < k1) cache[i - k0] = bi;
-                if (j >= k0 && j < k1) cache[j - k0] = bj;
-                sh.sel = g;
-                sh.decision = (peer_slot<CLUSTER>(sh, par, 0)->flags & 1) ? 2 : 0;
             }
             par ^= 1;
             __syncthreads();
+            LAP(6);
             if (sh.decision == 2) { status = PJAC_ETIMEOUT; break; }
         }
+#undef LAP
+        if (rank == 0 && tid == 0) PROF_ADD(10, rot);
         if (tid == 0) last_score = sh.sel.key == KEY_NONE ? 0.0 :
                           (pivot == PJAC_PIVOT_GREEDY ? fabs(sh.sel.x) : cand_value(sh.sel, pivot, diag));
     }
@@ -637,11 +871,11 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
 
 size_t jacobi_smem_bytes(int n, int P) {
     int m = (n + P - 1) / P;
-    return (size_t)n * sizeof(double) + (size_t)m * sizeof(Cand) + (size_t)m * sizeof(int) + 16;
+    return (size_t)n * sizeof(double) + 2 * (size_t)m * sizeof(Cand) + (size_t)m * sizeof(int) + 16;
 }
 
 template <bool CLUSTER>
-__global__ void __launch_bounds__(NT) jacobi_single_kernel(JacArgs a) {
+__global__ void __launch_bounds__(NT, 1) jacobi_single_kernel(JacArgs a) {
     __shared__ Sh sh;
     extern __shared__ __align__(16) unsigned char dyn[];
     int P = 1, rank = 0;
@@ -653,8 +887,9 @@ __global__ void __launch_bounds__(NT) jacobi_single_kernel(JacArgs a) {
     int m = (a.n + P - 1) / P;
     double* diag = reinterpret_cast<double*>(dyn);
     Cand* cache = reinterpret_cast<Cand*>(diag + a.n);
-    int* resc = reinterpret_cast<int*>(cache + m);
-    jacobi_problem<CLUSTER>(a, rank, P, sh, diag, cache, resc);
+    Cand* cache2 = cache + m;
+    int* resc = reinterpret_cast<int*>(cache2 + m);
+    jacobi_problem<CLUSTER>(a, rank, P, sh, diag, cache, cache2, resc);
 }
 
 // Batched form: each CTA takes problems from a queue (largest first).
@@ -680,8 +915,9 @@ __global__ void __launch_bounds__(NT) jacobi_batched_kernel(const BatchDesc* des
         a.check_every = d.n; a.budget_cycles = budget_cycles; a.info = d.info;
         double* diag = reinterpret_cast<double*>(dyn);
         Cand* cache = reinterpret_cast<Cand*>(diag + d.n);
-        int* resc = reinterpret_cast<int*>(cache + d.n);
-        jacobi_problem<false>(a, 0, 1, sh, diag, cache, resc);
+        Cand* cache2 = cache + d.n;
+        int* resc = reinterpret_cast<int*>(cache2 + d.n);
+        jacobi_problem<false>(a, 0, 1, sh, diag, cache, cache2, resc);
         __syncthreads();
     }
 }
@@ -853,6 +1089,17 @@ __global__ void info_single_kernel(const DevInfo* src, pjac_info* dst) {
     o.ms_jacobi = 0.f;
     *dst = o;
 }
+
+#ifdef PJAC_PROFILE
+extern "C" int pjac_prof_read(unsigned long long* out, int reset) {
+    cudaMemcpyFromSymbol(out, g_prof, sizeof(unsigned long long) * 16);
+    if (reset) {
+        unsigned long long z[16] = {0};
+        cudaMemcpyToSymbol(g_prof, z, sizeof(z));
+    }
+    return 0;
+}
+#endif
 
 cudaError_t launch_info_single(const DevInfo* src, pjac_info* dst, cudaStream_t st) {
     info_single_kernel<<<1, 1, 0, st>>>(src, dst);
