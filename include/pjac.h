@@ -149,6 +149,32 @@ int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int lda1, const
                               int ldv, pjac_info* info, void* stream);
 
 /*
+ * Allocation-free variant of pjac_solve_preconditioned.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory at solve time -- a process that reserves its whole device
+ * memory budget when it starts (its own allocator then holds all free
+ * memory, so a cudaMalloc during a solve would fail or fragment it), or a
+ * plug-in that runs inside a host application without access to that
+ * application's allocator.  It needs no handle and allocates nothing: its
+ * scratch lives in a fixed array of PJAC_NOALLOC_SCRATCH_BYTES that the
+ * library places in every GPU's memory when it is loaded, and keeps there
+ * until the process exits.
+ *   Arguments, layouts and results are those of pjac_solve_preconditioned
+ *   with the default options (off-diagonal stop at tol).
+ *   n must not exceed PJAC_NOALLOC_MAX_N; larger n returns PJAC_EINVAL.
+ *   The first call on a device looks up the array's device address; make
+ *   that first call before any stream capture on that device.
+ *   All calls share the one array: calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race on it and must be serialised
+ *   by the caller.  The call synchronises the stream.
+ */
+#define PJAC_NOALLOC_MAX_N 512
+#define PJAC_NOALLOC_SCRATCH_BYTES ((size_t)PJAC_NOALLOC_MAX_N * PJAC_NOALLOC_MAX_N * 8 + 8192)
+int pjac_solve_preconditioned_noalloc(double* A1, int n, int lda1, const double* V0, int ldv0,
+                                      pjac_pivot pivot, double tol, double* W, double* V, int ldv,
+                                      pjac_info* info, void* stream);
+
+/*
  * Batched form: nb independent problems of order n[p] (2 <= n[p] <= 1024)
  * packed in one device buffer.  Host arrays n, a_off, w_off, v_off give each
  * problem's order and its offsets (in doubles) into A, W and V; problem p is

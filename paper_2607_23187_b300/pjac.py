@@ -32,6 +32,7 @@ EXPORTS = (
     "pjac_solve", "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_default_opts",
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
+    "pjac_solve_preconditioned_noalloc",
 )
 
 
