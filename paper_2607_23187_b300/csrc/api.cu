@@ -228,14 +228,31 @@ static int product(pjac_handle* h, bool ta, bool tb, int n, double alpha, const 
 static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda, const float* Q0,
                            double* Q, long long ldq, double* A1, long long lda1, SolveWs& w, cudaStream_t st) {
     CK(cudaEventRecord(h->ev[0], st));
-    const float* q0 = Q0;
-    long long ldq0 = n;
-    if (!q0) {
+    if (Q0) {
+        // X = fl64(Q0) as given
+        CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
+    } else {
+        // FP32 spectral decomposition of fl32(A).  FP32 Jacobi accumulates
+        // rounding over its many rotation layers, leaving Q0 about
+        // sqrt(layers) * u_32 from an eigenbasis; one refinement pass on
+        // B = fl32(Q0^T A Q0) (formed with FP64 products, nearly diagonal, so
+        // its rotations are small and converge in a few sweeps) brings the
+        // decomposition to A = Q0 Lambda Q0^T + O(||A|| u_32), the accuracy
+        // Sec. 2.1 asks of the low-precision decomposition.
         CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, st));
-        q0 = w.Q0;
+        CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                       // X = fl64(Q0)
+        int r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);   // T = A X
+        if (r) return r;
+        r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);        // Y = X^T A X
+        if (r) return r;
+        CK(symmetrize(w.Y, n, n, st));
+        CK(diag_fp32(w.Y, n, n, w.Q0, w.d32, nullptr, 40, st));             // Q_fix
+        CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
+        r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);       // X Q_fix
+        if (r) return r;
+        CK(copy_f64(w.Y, n, Q, ldq, n, n, st));
     }
-    // X = fl64(Q0);  X <- X (3I - X^T X) / 2
-    CK(copy_f32_to_f64(q0, ldq0, Q, ldq, n, st));
+    // X <- X (3I - X^T X) / 2
     int steps = h->opts.ns_steps;
     for (int it = 0; it < steps; ++it) {
         int r = product(h, true, false, n, 1.0, Q, ldq, Q, ldq, 0.0, w.Y, n, st);

@@ -65,6 +65,33 @@ __device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
     return r;
 }
 
+// Exact Eq. (1.1) score and the rotation of pivot (i, j), i < j, from one
+// shared denominator: l equals gap_exact(dii, djj, q) and (c, s, t) equal
+// rot_params(dii, djj, q), bit for bit (the score depends on |d| only).
+struct Eval { double l, c, s, t; };
+
+__device__ __forceinline__ Eval eval_pair(double dii, double djj, double q) {
+    Eval r;
+    if (q == 0.0) { r.l = 0.0; r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
+    double d = __dadd_rn(dii, -djj);
+    int e = scale_exp(d, q);
+    if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
+    double q2 = __dmul_rn(q, q);
+    double q4 = __dmul_rn(4.0, q2);
+    double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(d, d), q4));
+    double den = __dadd_rn(fabs(d), rr);
+    double l = __ddiv_rn(__dmul_rn(2.0, q2), den);
+    if (e != 0) l = ldexp(l, e);
+    double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
+    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    double c = __ddiv_rn(den, __dsqrt_rn(__dadd_rn(__dmul_rn(den, den), q4)));
+    r.l = l;
+    r.t = t;
+    r.c = c;
+    r.s = __dmul_rn(t, c);
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Screen keys.  Selecting the pivot needs the exact argmax of the FP64
 // scores (ties to the smallest index), but an FP64 square root and division
@@ -72,16 +99,16 @@ __device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
 // computed with integer and FP32 instructions; only entries whose key lies
 // within KEY_TIE of the best key are evaluated exactly.
 //
-// Gap rule: key = floor(2^20 * log2(L~)) with |log2 L~ - log2 L| <= 2^-17
-// + 2^-21: mantissas truncated to 23 bits (2^-23 relative each), a handful
-// of correctly rounded FP32 operations, and __log2f, whose error is at most
-// 2 ulp of its result (|result| <= 64, so <= 2^-17 absolute); the
-// asymptotic forms below are exact to 2^-118.  The key is therefore within
-// 10 units of 2^20 log2 L, and KEY_GAP_TIE = 64 units keeps a 3x margin over
-// twice that: an entry whose key is more than KEY_GAP_TIE below another's
-// has a strictly smaller FP64 score.  When the best key is below 2^-500,
-// where FP64 scores lose relative accuracy to underflow, every entry is
-// evaluated exactly.
+// Gap rule: key = floor(2^20 * log2(L~)).  Error budget of log2 L~:
+// mantissas truncated to 23 bits (2^-23 relative each), the FP32 quotient,
+// square root and reciprocal taken from the fast approximations (__fdividef
+// and rsqrtf, each within 2 ulp) plus a few correctly rounded FP32
+// operations -- about 12 ulp = 12 * 2^-24 relative in all, 2^-19.5 in log2
+// -- and __log2f, within 2 ulp of a result of magnitude <= 64 (<= 2^-17
+// absolute).  The key is therefore within 12 units of 2^20 log2 L, and
+// KEY_GAP_TIE = 64 units keeps more than a 2x margin over twice that: an
+// entry whose key is more than KEY_GAP_TIE below another's has a strictly
+// smaller FP64 score.  The asymptotic forms below are exact to 2^-118.
 // Greedy rule: key = high 32 bits of |x| (monotone in |x|); entries with the
 // same key are compared on the full |x|.
 // ---------------------------------------------------------------------------
@@ -124,13 +151,14 @@ __device__ __forceinline__ int gap_key(double x, double dd) {
         int e = ed - ex;
         if (e >= 60) {             // L ~ x^2/|d|
             ip = 2 * exu - (ed - 1023 - adj);
-            f = __log2f(__fdiv_rn(mx * mx, md));
+            f = __log2f(__fdividef(mx * mx, md));
         } else if (e <= -60) {     // L ~ |x|
             ip = exu;
             f = __log2f(mx);
         } else {
-            float rho = __fdiv_rn(md, mx) * __int_as_float((e + 127) << 23);
-            float g = __fdiv_rn(2.0f, rho + __fsqrt_rn(__fmaf_rn(rho, rho, 4.0f)));
+            float rho = __fdividef(md, mx) * __int_as_float((e + 127) << 23);
+            float v = __fmaf_rn(rho, rho, 4.0f);
+            float g = __fdividef(2.0f, rho + v * rsqrtf(v));
             ip = exu;
             f = __log2f(mx * g);
         }

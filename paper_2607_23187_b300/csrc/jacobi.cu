@@ -40,7 +40,8 @@ struct Cand {
 };
 
 struct Slot {
-    Cand loc, pi, pj;
+    Cand loc, pi, pj;       // this CTA's best own row, its part of row i, of row j
+    double prm[3][3];       // (c, s, t) of the rotation of each of the three
     double sum;
     int flags, pad;
 };
@@ -55,6 +56,7 @@ struct Sh {
     Cand out;
     Slot slots[2];
     Slot inbox[2][16];      // slot of every cluster rank, pushed by the sender
+    Slot stage;             // this CTA's slot before it is pushed
     Cand sel;
     int tflag, pad3;
     double c, s, t, dii, djj, q;
@@ -65,8 +67,13 @@ struct Sh {
 
 #ifdef PJAC_PROFILE
 // Profiling build only: per-phase clock totals of CTA 0 and event counts.
-__device__ unsigned long long g_prof[16];
+__device__ unsigned long long g_prof[24];
 #define PROF_ADD(k, v) atomicAdd(&g_prof[k], (unsigned long long)(v))
+// exact evaluations made by this CTA (one counter per CTA)
+__device__ __forceinline__ unsigned int& prof_exact() {
+    __shared__ unsigned int s;
+    return s;
+}
 #else
 #define PROF_ADD(k, v) ((void)0)
 #endif
@@ -89,7 +96,9 @@ __device__ __forceinline__ double cand_value(Cand& c, int pivot, const double* d
     if (pivot == PJAC_PIVOT_GREEDY) return fabs(c.x);
     if (c.ex < 0.0) {
         c.ex = gap_exact(diag[c.row], diag[c.col], c.x);
-        PROF_ADD(8, 1);
+#ifdef PJAC_PROFILE
+        if (c.x != 0.0) atomicAdd(&prof_exact(), 1u);
+#endif
     }
     return c.ex;
 }
@@ -292,8 +301,8 @@ __device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const dou
 
 // Best candidate over the first `width` lanes of a warp (width a power of
 // two <= 32; butterfly, every lane of the group ends with the maximum).  The
-// row and column travel packed in one word; a received candidate's exact
-// score is recomputed if a comparison needs it.
+// row and column travel packed in one word, with the candidate's exact
+// score (when known) and its origin tag (pad).
 __device__ __forceinline__ Cand warp_best(Cand c, int width, int pivot, const double* diag) {
     for (int off = width >> 1; off > 0; off >>= 1) {
         Cand o;
@@ -301,9 +310,9 @@ __device__ __forceinline__ Cand warp_best(Cand c, int width, int pivot, const do
         int rc = __shfl_xor_sync(0xffffffffu, (c.row << 16) | (c.col & 0xffff), off);
         o.row = rc >> 16;
         o.col = rc & 0xffff;
-        o.pad = 0;
+        o.pad = __shfl_xor_sync(0xffffffffu, c.pad, off);
         o.x = __shfl_xor_sync(0xffffffffu, c.x, off);
-        o.ex = -1.0;
+        o.ex = __shfl_xor_sync(0xffffffffu, c.ex, off);
         if (o.key == KEY_NONE) { o.row = -1; o.col = -1; }
         if (better(o, c, pivot, diag)) c = o;
     }
@@ -421,7 +430,11 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     long long start = clock64();
 #ifdef PJAC_PROFILE
     long long pt = clock64();
-#define LAP(k) do { if (rank == 0 && tid == 0) { long long nw = clock64(); PROF_ADD(k, nw - pt); pt = nw; } } while (0)
+    unsigned int pex = 0;
+    if (tid == 0) prof_exact() = 0;
+    __syncthreads();
+#define LAP(k) do { if (rank == 0 && tid == 0) { long long nw = clock64(); PROF_ADD(k, nw - pt); pt = nw; \
+        unsigned int ce = prof_exact(); PROF_ADD(12 + (k), ce - pex); pex = ce; } } while (0)
 #else
 #define LAP(k) ((void)0)
 #endif
@@ -683,6 +696,77 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; }
         }
         __syncthreads();
+        // Publish this CTA's three candidates (best own row, its part of row
+        // i, its part of row j) with their exact scores and rotations --
+        // evaluated by three lanes at once, from one shared denominator --
+        // push them into every rank's inbox, and select after the cluster
+        // barrier.  Every CTA ends with the same winner in sh.sel and its
+        // rotation in sh.c, sh.s, sh.t; the owners of rows i and j take
+        // those rows' new bests.  i, j < 0: no rows i, j (first selection).
+        auto publish_select = [&](Cand loc, Cand pI, Cand pJ, int i, int j) {
+            if (tid < 3) {
+                Cand c = (tid == 0) ? loc : (tid == 1 ? pI : pJ);
+                double pc = 1.0, ps = 0.0, pt = 0.0;
+                if (c.key != KEY_NONE) {
+                    int ci = min(c.row, c.col), cj = max(c.row, c.col);
+                    Eval ev = eval_pair(diag[ci], diag[cj], c.x);
+                    if (pivot != PJAC_PIVOT_GREEDY) c.ex = ev.l;
+                    pc = ev.c;
+                    ps = ev.s;
+                    pt = ev.t;
+                }
+                if (tid == 0) sh.stage.loc = c;
+                else if (tid == 1) sh.stage.pi = c;
+                else sh.stage.pj = c;
+                sh.stage.prm[tid][0] = pc;
+                sh.stage.prm[tid][1] = ps;
+                sh.stage.prm[tid][2] = pt;
+                if (tid == 0) { sh.stage.sum = 0.0; sh.stage.flags = sh.tflag; sh.stage.pad = 0; }
+            }
+            __syncwarp();
+            if (tid < P) {
+                if (CLUSTER) {
+                    cg::cluster_group cl = cg::this_cluster();
+                    *cl.map_shared_rank(&sh.inbox[par][rank], tid) = sh.stage;
+                } else {
+                    sh.inbox[par][0] = sh.stage;
+                }
+            }
+            cta_exchange_sync<CLUSTER>();
+            LAP(5);
+            const int warp = tid >> 5, lane = tid & 31;
+            int width = 1;
+            while (width < P) width <<= 1;
+            if (warp < 3) {
+                Cand c = no_cand();
+                if (lane < P) {
+                    const Slot& sl = sh.inbox[par][lane];
+                    c = (warp == 0) ? sl.loc : (warp == 1 ? sl.pi : sl.pj);
+                    c.pad = lane * 3 + warp;
+                }
+                c = warp_best(c, width, pivot, diag);
+                if (lane == 0) sh.out3[warp] = c;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                Cand g = sh.out3[0], bi = sh.out3[1], bj = sh.out3[2];
+                if (better(bi, g, pivot, diag)) g = bi;
+                if (better(bj, g, pivot, diag)) g = bj;
+                if (i >= k0 && i < k1) { cache[i - k0] = bi; cache2[i - k0] = no_cand(); }
+                if (j >= k0 && j < k1) { cache[j - k0] = bj; cache2[j - k0] = no_cand(); }
+                if (g.key != KEY_NONE) {
+                    const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
+                    sh.c = pr[0];
+                    sh.s = pr[1];
+                    sh.t = pr[2];
+                }
+                sh.sel = g;
+                sh.decision = (sh.inbox[par][0].flags & 1) ? 2 : 0;
+            }
+            par ^= 1;
+            __syncthreads();
+        };
+
         // first selection
         {
             Cand loc = no_cand();
@@ -693,23 +777,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 Cand c = cache[k - k0];
                 if (better(c, loc, pivot, diag)) loc = c;
             }
+            if (tid == 0) sh.tflag = 0;
             loc = block_select(loc, pivot, diag, sh);
-            if (tid == 0) {
-                sh.slots[par].loc = loc;
-                sh.slots[par].pi = no_cand();
-                sh.slots[par].pj = no_cand();
-            }
-            cta_exchange_sync<CLUSTER>();
-            if (tid == 0) {
-                Cand g = no_cand();
-                for (int r = 0; r < P; ++r) {
-                    Cand c = peer_slot<CLUSTER>(sh, par, r)->loc;
-                    if (better(c, g, pivot, diag)) g = c;
-                }
-                sh.sel = g;
-            }
-            par ^= 1;
-            __syncthreads();
+            publish_select(loc, no_cand(), no_cand(), -1, -1);
         }
         bool stop_now = false;
         for (;;) {
@@ -723,7 +793,8 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 Cand g0 = sh.sel;
                 if (g0.key != KEY_NONE) preload(min(g0.row, g0.col), max(g0.row, g0.col));
             }
-            // decisions on the current selection (thread 0, then broadcast)
+            // decisions on the current selection (thread 0, then broadcast);
+            // its exact score and rotation arrived with it
             if (tid == 0) {
                 Cand g = sh.sel;
                 int dec = 0;
@@ -733,27 +804,20 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     v = fabs(g.x);
                     if (v == 0.0) dec = 1;
                 } else {
-                    if (g.key == KEY_ZERO) { v = 0.0; dec = 1; }
-                    else if (g.key < KEY_SUB) { v = cand_value(g, pivot, diag); if (v == 0.0) dec = 1; }
-                    if (!dec && a.stop == PJAC_STOP_LIBOUND) {
-                        long long dk = (long long)g.key - (long long)sh.key_eps;
-                        if (dk <= KEY_GAP_TIE) {
-                            v = cand_value(g, pivot, diag);
-                            if (v <= sh.eps_li) dec = 1;
-                        }
-                    }
+                    v = cand_value(g, pivot, diag);
+                    if (v == 0.0) dec = 1;
+                    if (!dec && a.stop == PJAC_STOP_LIBOUND && v <= sh.eps_li) dec = 1;
                 }
                 if (!dec && rot >= a.max_rot) dec = 3;
-                if (v >= 0.0) sh.q = v;   // remember exact score when known
+                if (v >= 0.0) sh.q = v;
                 sh.decision = dec;
                 if (!dec) {
                     int i = min(g.row, g.col), j = max(g.row, g.col);
                     double q = g.x;
-                    Rot rp = rot_params(diag[i], diag[j], q);
-                    sh.pi = i; sh.pj = j;
-                    sh.c = rp.c; sh.s = rp.s;
-                    sh.dii = __fma_rn(rp.t, q, diag[i]);
-                    sh.djj = __fma_rn(-rp.t, q, diag[j]);
+                    sh.pi = i;
+                    sh.pj = j;
+                    sh.dii = __fma_rn(sh.t, q, diag[i]);
+                    sh.djj = __fma_rn(-sh.t, q, diag[j]);
                     diag[i] = sh.dii;
                     diag[j] = sh.djj;
                 }
@@ -794,47 +858,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             }
             block_select3(loc, pI, pJ, pivot, diag, sh);
             LAP(4);
-            // push this CTA's slot into every rank's inbox (remote stores
-            // before the barrier), then reduce locally after it
-            if (tid < P) {
-                Slot my;
-                my.loc = loc; my.pi = pI; my.pj = pJ; my.sum = 0.0; my.flags = sh.tflag; my.pad = 0;
-                if (CLUSTER) {
-                    cg::cluster_group cl = cg::this_cluster();
-                    *cl.map_shared_rank(&sh.inbox[par][rank], tid) = my;
-                } else {
-                    sh.inbox[par][0] = my;
-                }
-            }
-            cta_exchange_sync<CLUSTER>();
-            LAP(5);
-            // three warps reduce the three kinds of candidates in parallel
-            {
-                const int warp = tid >> 5, lane = tid & 31;
-                int width = 1;
-                while (width < P) width <<= 1;
-                if (warp < 3) {
-                    Cand c = no_cand();
-                    if (lane < P) {
-                        const Slot& sl = sh.inbox[par][lane];
-                        c = (warp == 0) ? sl.loc : (warp == 1 ? sl.pi : sl.pj);
-                    }
-                    c = warp_best(c, width, pivot, diag);
-                    if (lane == 0) sh.out3[warp] = c;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    Cand g = sh.out3[0], bi = sh.out3[1], bj = sh.out3[2];
-                    if (better(bi, g, pivot, diag)) g = bi;
-                    if (better(bj, g, pivot, diag)) g = bj;
-                    if (i >= k0 && i < k1) { cache[i - k0] = bi; cache2[i - k0] = no_cand(); }
-                    if (j >= k0 && j < k1) { cache[j - k0] = bj; cache2[j - k0] = no_cand(); }
-                    sh.sel = g;
-                    sh.decision = (sh.inbox[par][0].flags & 1) ? 2 : 0;
-                }
-            }
-            par ^= 1;
-            __syncthreads();
+            publish_select(loc, pI, pJ, i, j);
             LAP(6);
             if (sh.decision == 2) { status = PJAC_ETIMEOUT; break; }
         }
@@ -1092,9 +1116,9 @@ __global__ void info_single_kernel(const DevInfo* src, pjac_info* dst) {
 
 #ifdef PJAC_PROFILE
 extern "C" int pjac_prof_read(unsigned long long* out, int reset) {
-    cudaMemcpyFromSymbol(out, g_prof, sizeof(unsigned long long) * 16);
+    cudaMemcpyFromSymbol(out, g_prof, sizeof(unsigned long long) * 24);
     if (reset) {
-        unsigned long long z[16] = {0};
+        unsigned long long z[24] = {0};
         cudaMemcpyToSymbol(g_prof, z, sizeof(z));
     }
     return 0;
