@@ -135,14 +135,6 @@ def max_over_ranks(ws, v):
     return float(t.item())
 
 
-def launches_per_solve(n, ns_steps=3):
-    """Kernels of ours launched by one pjac_solve (fixed by the pipeline):
-    input check 1, FP32 diagonaliser 1 (cooperative), FP32->FP64 copy 1,
-    Newton-Schulz 4 per step, transform 2 + symmetrise 1, Jacobi 1,
-    readout 2."""
-    return 1 + 1 + 1 + 4 * ns_steps + 3 + 1 + 2
-
-
 def bench_config(args, n):
     """The workload description both arms print."""
     return {"workload": "%s: n=%d, gap rule, off-diagonal stop 1e-15 ||A1||_F, eigenvalues and vectors"
@@ -357,7 +349,7 @@ def run_ours(args, ws, rank, local):
            "extras": extras,
            "e2e": {"value": ws / (e2e_ms / 1000.0), "unit": "solves/s",
                    "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n + 8 * n * n},
-           "gpu_launches": launches_per_solve(n) * args.steps,
+           "gpu_launches": pjac.load().pjac_solve_launch_count(h.h, n) * args.steps,
            "roofline": roof,
            "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
@@ -377,7 +369,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
     ap.add_argument("--with-4096", action="store_true", help="add one timed n=4096 (cfg3) solve")
-    ap.add_argument("--transform", default="fp64", choices=["fp64", "split_bf16"])
+    ap.add_argument("--transform", default="split_bf16", choices=["split_bf16", "fp64"])
     ap.add_argument("--ref-rotations", type=int, default=100000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

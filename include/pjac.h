@@ -126,6 +126,34 @@ int pjac_precondition(pjac_handle* h, const double* A, int n, int lda, const flo
                       double* Q, int ldq, double* A1, int lda1, void* stream);
 
 /*
+ * Working-precision product C = alpha op(A) op(B) + beta C, computed the way
+ * the preconditioner of Sec. 2.1 computes its products (the Newton--Schulz
+ * steps and Q^T A Q), with the handle's transform option:
+ *   PJAC_TRANSFORM_SPLIT_BF16: the operands are cut into 6-bit (5-bit for
+ *     k > 4227) digit slices scaled per row of op(A) and per column of
+ *     op(B); slice products run on the tensor cores in BF16 with exact FP32
+ *     accumulation and are summed exactly in 64-bit fixed point (Ozaki, Ogita,
+ *     Oishi and Rump's error-free splitting).  Error per entry at most
+ *     |alpha| 2^(e_i+f_j) (k (S+3) 2^(-bS) + 2^-47) + 2^-53 |C_ij|, where
+ *     2^(e_i-1) <= max_l |op(A)_il| < 2^e_i, likewise f_j for op(B)'s
+ *     column j, and b S = 54 (b = 6, S = 9) or 55 (b = 5, S = 11).
+ *   PJAC_TRANSFORM_FP64: plain FP64 products on the CUDA cores.
+ * All matrices are FP64, column-major, in device memory.
+ *   transa, transb  0: op(X) = X, 1: op(X) = X^T.
+ *   m, n, k         op(A) is m x k, op(B) is k x n, C is m x n; 1..PJAC_MAX_N.
+ *   lda >= rows of A as stored (m, or k if transposed); likewise ldb; ldc >= m.
+ *   beta == 0: C is not read.  C must not overlap A or B.  Entries of A
+ *   and B must be finite.
+ * Synchronises the stream (it reads the product's device status).
+ * Errors: PJAC_EINVAL, PJAC_ENOMEM, PJAC_ENOTIMPL (k > 17458 with the split
+ * product), PJAC_ETIMEOUT (a wait inside the tensor-core pipeline timed
+ * out; C is unspecified), PJAC_ECUDA.
+ */
+int pjac_product(pjac_handle* h, int transa, int transb, int m, int n, int k, double alpha,
+                 const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                 void* stream);
+
+/*
  * Full solve: preconditioner, then Algorithm 1 on A1 with V0 = Q, then the
  * readout (W ascending, V's columns in the same order).
  *   A   [in]  n x n symmetric, not modified.
@@ -237,6 +265,12 @@ typedef struct {
     size_t peak_hbm_bytes;
 } pjac_serve_stats;
 int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
+
+/* Number of kernel launches of this library that one pjac_solve of size n
+ * makes with the handle's current options (preconditioner products,
+ * element-wise steps, the Jacobi kernel, the readout).  A diagnostic for
+ * launch accounting; returns -1 when h is NULL or n is out of range. */
+int pjac_solve_launch_count(pjac_handle* h, int n);
 
 /* Human-readable text for a status code (static storage). */
 const char* pjac_status_string(int status);

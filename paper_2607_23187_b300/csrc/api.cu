@@ -72,7 +72,7 @@ extern "C" void pjac_default_opts(pjac_opts* o) {
     o->tol = 1e-15;
     o->max_rotations = 0;
     o->check_every = 0;
-    o->transform = PJAC_TRANSFORM_FP64;
+    o->transform = PJAC_TRANSFORM_SPLIT_BF16;
     o->ns_steps = 3;
     o->cluster_size = 0;
     o->time_budget_s = 600.0;
@@ -203,57 +203,57 @@ static int layout_ws(pjac_handle* h, int n, SolveWs* w) {
     return PJAC_OK;
 }
 
-// C = op(A) op(B) with the product chosen by the options.
-static int product(pjac_handle* h, bool ta, bool tb, int n, double alpha, const double* A, long long lda,
-                   const double* B, long long ldb, double beta, double* C, long long ldc, cudaStream_t st) {
-    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16) {
-        size_t need = gemm_split_bf16_ws(n, n, n);
-        if (need > 0) {
-            int r = h->tcws.ensure(need);
-            if (r) return r;
-            cudaError_t e = gemm_split_bf16(ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, h->tcws.p,
-                                            h->tcws.bytes, st);
-            if (e == cudaSuccess) return PJAC_OK;
-            if (e != cudaErrorNotSupported) return cuda_err(e, "gemm_split_bf16");
-            cudaGetLastError();
-            return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available for this shape");
-        }
-        return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available");
-    }
-    CK(gemm_f64(ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, st));
+// Tensor-core products: size the workspace for m x n x k products and clear
+// their device status word.  Called before a sequence of products.
+static int tc_prepare(pjac_handle* h, int m, int n, int k, cudaStream_t st) {
+    if (h->opts.transform != PJAC_TRANSFORM_SPLIT_BF16) return PJAC_OK;
+    size_t need = gemm_split_bf16_ws(m, n, k);
+    if (need == 0)
+        return set_err(PJAC_ENOTIMPL, "split-BF16 product not available for inner dimension %d", k);
+    int r = h->tcws.ensure(need);
+    if (r) return r;
+    CK(cudaMemsetAsync(gemm_split_bf16_errflag(h->tcws.p), 0, sizeof(int), st));
     return PJAC_OK;
 }
 
-// Sec. 2.1 into workspace: Q (ld n) and A1 (ld n).  Records ev[0..2].
-static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda, const float* Q0,
-                           double* Q, long long ldq, double* A1, long long lda1, SolveWs& w, cudaStream_t st) {
-    CK(cudaEventRecord(h->ev[0], st));
-    if (Q0) {
-        // X = fl64(Q0) as given
-        CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
-    } else {
-        // FP32 spectral decomposition of fl32(A).  FP32 Jacobi accumulates
-        // rounding over its many rotation layers, leaving Q0 about
-        // sqrt(layers) * u_32 from an eigenbasis; one refinement pass on
-        // B = fl32(Q0^T A Q0) (formed with FP64 products, nearly diagonal, so
-        // its rotations are small and converge in a few sweeps) brings the
-        // decomposition to A = Q0 Lambda Q0^T + O(||A|| u_32), the accuracy
-        // Sec. 2.1 asks of the low-precision decomposition.
-        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, st));
-        CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                       // X = fl64(Q0)
-        int r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);   // T = A X
-        if (r) return r;
-        r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);        // Y = X^T A X
-        if (r) return r;
-        CK(symmetrize(w.Y, n, n, st));
-        CK(diag_fp32(w.Y, n, n, w.Q0, w.d32, nullptr, 40, st));             // Q_fix
-        CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
-        r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);       // X Q_fix
-        if (r) return r;
-        CK(copy_f64(w.Y, n, Q, ldq, n, n, st));
+// Device status of the tensor-core products since tc_prepare (synchronises).
+static int tc_status(pjac_handle* h, cudaStream_t st) {
+    if (h->opts.transform != PJAC_TRANSFORM_SPLIT_BF16) return PJAC_OK;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, gemm_split_bf16_errflag(h->tcws.p), sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) return set_err(PJAC_ETIMEOUT, "tensor-core product pipeline timed out (code %d)", flag);
+    return PJAC_OK;
+}
+
+// C = alpha op(A) op(B) + beta C with the product chosen by the options
+// (the split-BF16 workspace was prepared by tc_prepare for this shape).
+static int product_mnk(pjac_handle* h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+                       long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
+                       cudaStream_t st) {
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16) {
+        cudaError_t e = gemm_split_bf16(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, h->tcws.p,
+                                        h->tcws.bytes, st);
+        if (e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available for this shape");
+        }
+        CK(e);
+        return PJAC_OK;
     }
-    // X <- X (3I - X^T X) / 2
-    int steps = h->opts.ns_steps;
+    CK(gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st));
+    return PJAC_OK;
+}
+
+static int product(pjac_handle* h, bool ta, bool tb, int n, double alpha, const double* A, long long lda,
+                   const double* B, long long ldb, double beta, double* C, long long ldc, cudaStream_t st) {
+    return product_mnk(h, ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, st);
+}
+
+// X <- X (3I - X^T X) / 2, steps times (Newton--Schulz; Sec. 2.1 names it
+// as one way to restore orthogonality to working precision).
+static int newton_schulz(pjac_handle* h, double* Q, long long ldq, int n, int steps, SolveWs& w,
+                         cudaStream_t st) {
     for (int it = 0; it < steps; ++it) {
         int r = product(h, true, false, n, 1.0, Q, ldq, Q, ldq, 0.0, w.Y, n, st);
         if (r) return r;
@@ -262,9 +262,48 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         if (r) return r;
         CK(copy_f64(w.T, n, Q, ldq, n, n, st));
     }
+    return PJAC_OK;
+}
+
+// Sec. 2.1 into workspace: Q (ld n) and A1 (ld n).  Records ev[0..2].
+static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda, const float* Q0,
+                           double* Q, long long ldq, double* A1, long long lda1, SolveWs& w, cudaStream_t st) {
+    int rp = tc_prepare(h, n, n, n, st);
+    if (rp) return rp;
+    CK(cudaEventRecord(h->ev[0], st));
+    if (Q0) {
+        // X = fl64(Q0) as given
+        CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
+    } else {
+        // FP32 spectral decomposition of fl32(A) (Sec. 2.1 with u_l = single,
+        // as in Sec. 4).  The parallel-order FP32 Jacobi pass leaves its
+        // basis off by the rounding of its many rotation layers, in the
+        // eigenvectors and in orthogonality (each FP32 rotation moves column
+        // norms by a rounding unit).  So: X = fl64(Q0) made orthogonal
+        // (Newton--Schulz), then a refinement pass on B = X^T fl32(A) X
+        // that diagonalises it further, X <- X (I + D).  After the final
+        // reorthogonalisation below, fl32(A) = Q Lambda Q^T to FP32 accuracy.
+        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, st));
+        CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
+        int r = newton_schulz(h, Q, ldq, n, 2, w, st);
+        if (r) return r;
+        CK(round_to_fp32(A, lda, w.Y, n, n, st));                             // Y = fl32(A)
+        r = product(h, false, false, n, 1.0, w.Y, n, Q, ldq, 0.0, w.T, n, st);    // T = fl32(A) X
+        if (r) return r;
+        r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
+        if (r) return r;
+        CK(symmetrize(w.Y, n, n, st));
+        CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, st));                        // D
+        CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
+        r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);    // X D
+        if (r) return r;
+        CK(add_f64(Q, ldq, w.Y, n, n, st));                                   // X (I + D)
+    }
+    int r = newton_schulz(h, Q, ldq, n, h->opts.ns_steps, w, st);
+    if (r) return r;
     CK(cudaEventRecord(h->ev[1], st));
     // A1 = Q^T (A Q), symmetrised
-    int r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);
+    r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);
     if (r) return r;
     r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
     if (r) return r;
@@ -287,7 +326,28 @@ extern "C" int pjac_precondition(pjac_handle* h, const double* A, int n, int lda
     if (r) return r;
     r = check_input(h, A, lda, n, st, w.flag);
     if (r) return r;
-    return precondition_ws(h, A, n, lda, Q0, Q, ldq, A1, lda1, w, st);
+    r = precondition_ws(h, A, n, lda, Q0, Q, ldq, A1, lda1, w, st);
+    if (r) return r;
+    return tc_status(h, st);
+}
+
+extern "C" int pjac_product(pjac_handle* h, int transa, int transb, int m, int n, int k, double alpha,
+                            const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                            void* stream) {
+    if (!h || !A || !B || !C) return set_err(PJAC_EINVAL, "NULL argument");
+    if (m < 1 || n < 1 || k < 1 || m > PJAC_MAX_N || n > PJAC_MAX_N || k > PJAC_MAX_N)
+        return set_err(PJAC_EINVAL, "m, n, k = %d, %d, %d out of range [1, %d]", m, n, k, PJAC_MAX_N);
+    if ((transa != 0 && transa != 1) || (transb != 0 && transb != 1))
+        return set_err(PJAC_EINVAL, "transa and transb must be 0 or 1");
+    if (lda < (transa ? k : m) || ldb < (transb ? n : k) || ldc < m)
+        return set_err(PJAC_EINVAL, "leading dimension too small");
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = tc_prepare(h, m, n, k, st);
+    if (r) return r;
+    r = product_mnk(h, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    if (r) return r;
+    return tc_status(h, st);
 }
 
 static long long budget_cycles(const pjac_opts& o) {
@@ -378,6 +438,8 @@ static int solve_pipeline(pjac_handle* h, const double* A, int n, int lda, pjac_
     r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
     if (r) return r;
     CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16)
+        CK(gemm_split_bf16_fold_status(h->tcws.p, w.info, st));   // a timed-out product fails the solve
     CK(cudaEventRecord(h->ev[3], st));
     return PJAC_OK;
 }
@@ -451,6 +513,25 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
     CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
     CK(cudaEventRecord(h->ev[3], st));
     return finish_info(h, w.info, info, st, true);
+}
+
+extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
+    if (!h || n < 1 || n > PJAC_MAX_N) return -1;
+    if (n == 1) return 0;
+    const bool split = h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16;
+    const int P = split ? gemm_split_bf16_launches(n, n, n) : 1;   // launches per product
+    const int ns = h->opts.ns_steps;
+    // input check, FP32 diagonaliser, copy to FP64
+    int c = 3;
+    // Newton--Schulz before the refinement (2 steps) and after it (ns steps):
+    // two products, 3I - Y and a copy per step
+    c += (2 + ns) * (2 * P + 2);
+    // fl32(A), T = fl32(A) X, B = X^T T, symmetrise, refinement, copy, X D, add
+    c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
+    // transform (two products) and symmetrise, Jacobi, readout (two kernels)
+    c += 2 * P + 1 + 1 + 2;
+    if (split) c += 1;  // product status folded into the solve record
+    return c;
 }
 
 extern "C" const char* pjac_status_string(int s) {

@@ -201,9 +201,206 @@ __global__ void __launch_bounds__(256) diag32_coop_kernel(const double* __restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// Refinement of the FP32 eigenbasis.  FP32 Jacobi on fl32(A) accumulates
+// rounding over its many rotation layers and ends about sqrt(layers) * u_32
+// from an eigenbasis of fl32(A).  Given X = fl64(Q0) and
+// B = X^T fl64(fl32(A)) X (formed with FP64 products; nearly diagonal), a few
+// more parallel-order Jacobi sweeps on B finish the decomposition of
+// fl32(A): the off-diagonal part of B is kept in FP32 (its entries are
+// small, so their rounding is small), the diagonal in FP64, and the
+// accumulated rotation as E + D with E the permutation of the tournament
+// seats and D small in FP32.  Output D (n x n): X (I + D) is an eigenbasis
+// of fl32(A) to FP32 accuracy, the decomposition Sec. 2.1 asks for.
+// ---------------------------------------------------------------------------
+struct RefPair { float c, s, cm1, t, b; int pp, pq; };
+
+__device__ __forceinline__ void refine_tile(int bt, const float* __restrict__ O0, float* __restrict__ O1,
+                                            const float* __restrict__ D0, float* __restrict__ D1,
+                                            const double* __restrict__ dg0, double* __restrict__ dg1,
+                                            const int* __restrict__ pl0, int* __restrict__ pl1, int npad,
+                                            RefPair* pr_r, RefPair* pr_c) {
+    const int T = npad / 32;
+    const int m = npad / 2;
+    bool isO = bt < T * T;
+    if (!isO) bt -= T * T;
+    const int tr = bt % T, tc = bt / T;
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        int which = tid >> 4, k = tid & 15;
+        int pairpos = (which == 0 ? tc : tr) * 32 + 2 * k;
+        int sp = tour_sigma(pairpos, m), sq = tour_sigma(pairpos + 1, m);
+        float b = O0[sp + (long long)sq * npad];
+        RefPair r;
+        r.b = b;
+        r.pp = pl0[sp];
+        r.pq = pl0[sq];
+        if (b == 0.0f) {
+            r.c = 1.0f; r.s = 0.0f; r.cm1 = 0.0f; r.t = 0.0f;
+        } else {
+            double dd = dg0[sp] - dg0[sq];
+            float d = (float)dd;
+            float den = fabsf(d) + hypotf(d, 2.0f * b);
+            float t = 2.0f * fabsf(b) / den;
+            if (dd != 0.0 && ((dd < 0.0) != (b < 0.0f))) t = -t;
+            float c = rsqrtf(1.0f + t * t);
+            r.t = t;
+            r.c = c;
+            r.s = t * c;
+            r.cm1 = -(t * t) * (c * c) / (1.0f + c);    // c - 1 without cancellation
+        }
+        if (which == 0) pr_c[k] = r;
+        else pr_r[k] = r;
+    }
+    __syncthreads();
+    const int a = tid & 15, bb = tid >> 4;
+    const int rp = tr * 32 + 2 * a, cp = tc * 32 + 2 * bb;
+    const RefPair pc = pr_c[bb];
+    if (isO) {
+        const RefPair pa = pr_r[a];
+        int r0 = tour_sigma(rp, m), r1 = tour_sigma(rp + 1, m);
+        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
+        float z00, z01, z10, z11;
+        if (rp == cp) {
+            // diagonal block: its rotation moves b into the FP64 diagonal
+            z00 = z01 = z10 = z11 = 0.0f;
+            if (a == bb) {
+                double tb = (double)pa.t * (double)pa.b;
+                dg1[rp] = dg0[r0] + tb;
+                dg1[rp + 1] = dg0[r1] - tb;
+                pl1[rp] = pl0[r0];
+                pl1[rp + 1] = pl0[r1];
+            }
+        } else {
+            float x00 = O0[r0 + (long long)c0 * npad], x10 = O0[r1 + (long long)c0 * npad];
+            float x01 = O0[r0 + (long long)c1 * npad], x11 = O0[r1 + (long long)c1 * npad];
+            rot2x2_sym(pa.c, pa.s, pc.c, pc.s, x00, x01, x10, x11, z00, z01, z10, z11);
+        }
+        O1[rp + (long long)cp * npad] = z00;
+        O1[rp + 1 + (long long)cp * npad] = z10;
+        O1[rp + (long long)(cp + 1) * npad] = z01;
+        O1[rp + 1 + (long long)(cp + 1) * npad] = z11;
+    } else {
+        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
+        for (int r = tr * 32 + a; r < tr * 32 + 32; r += 16) {
+            float q0 = D0[r + (long long)c0 * npad], q1 = D0[r + (long long)c1 * npad];
+            float v0 = q0 * pc.c + q1 * pc.s;
+            float v1 = -q0 * pc.s + q1 * pc.c;
+            if (r == pc.pp) { v0 += pc.cm1; v1 -= pc.s; }
+            if (r == pc.pq) { v0 += pc.s; v1 += pc.cm1; }
+            D1[r + (long long)cp * npad] = v0;
+            D1[r + (long long)(cp + 1) * npad] = v1;
+        }
+    }
+    __syncthreads();
+}
+
+// ws layout (floats): O[2][npad^2], D[2][npad^2], then dg[2][npad] doubles,
+// pl[2][npad] ints, acc[4] doubles.
+__global__ void __launch_bounds__(256) refine32_coop_kernel(const double* __restrict__ B, int n, int npad,
+                                                            float* ws, float* Dout, int max_sweeps) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ RefPair pr_r[16], pr_c[16];
+    __shared__ double s_off[8], s_all[8];
+    const long long nn = (long long)npad * npad;
+    float* Ob[2] = {ws, ws + nn};
+    float* Db[2] = {ws + 2 * nn, ws + 3 * nn};
+    double* dgb0 = reinterpret_cast<double*>(ws + 4 * nn);
+    double* dgb[2] = {dgb0, dgb0 + npad};
+    int* plb0 = reinterpret_cast<int*>(dgb0 + 2 * npad);
+    int* plb[2] = {plb0, plb0 + npad};
+    double* acc = reinterpret_cast<double*>(plb0 + 2 * npad + 2);   // 8-byte aligned (npad even)
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long e = gtid; e < nn; e += gstride) {
+        int r = (int)(e % npad), c = (int)(e / npad);
+        Ob[0][e] = (r != c && r < n && c < n) ? (float)B[r + (long long)c * n] : 0.0f;
+        Db[0][e] = 0.0f;
+    }
+    for (long long e = gtid; e < npad; e += gstride) {
+        int p = (int)e;
+        dgb[0][p] = (p < n) ? B[p + (long long)p * n] : 0.0;
+        plb[0][p] = p;
+    }
+    if (gtid < 4) acc[gtid] = 0.0;
+    grid.sync();
+    const int T = npad / 32;
+    const int ntiles = 2 * T * T;
+    int cur = 0;
+    double prev = -1.0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int r = 0; r < npad - 1; ++r) {
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+                refine_tile(t, Ob[cur], Ob[cur ^ 1], Db[cur], Db[cur ^ 1], dgb[cur], dgb[cur ^ 1], plb[cur],
+                            plb[cur ^ 1], npad, pr_r, pr_c);
+            cur ^= 1;
+            grid.sync();
+        }
+        double off = 0.0, all = 0.0;
+        for (long long e = gtid; e < nn; e += gstride) {
+            double v = (double)Ob[cur][e];
+            off += v * v;
+        }
+        for (long long e = gtid; e < npad; e += gstride) {
+            double v = dgb[cur][e];
+            all += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if ((threadIdx.x & 31) == 0) { s_off[threadIdx.x >> 5] = off; s_all[threadIdx.x >> 5] = all; }
+        __syncthreads();
+        double* slot = acc + 2 * (sweep & 1);
+        if (threadIdx.x == 0) {
+            double o2 = 0, a2 = 0;
+            for (int w = 0; w < 8; ++w) { o2 += s_off[w]; a2 += s_all[w]; }
+            atomicAdd(slot, o2);
+            atomicAdd(slot + 1, a2);
+        }
+        grid.sync();
+        double o2 = __ldcg(slot), a2 = __ldcg(slot + 1);
+        // converged well past FP32 accuracy, or no longer improving.  The
+        // first sweeps of a poor start only shrink off(B) by a factor 2-3
+        // (linear phase until off(B) is below the cluster gaps), so the
+        // stagnation test waits for the quadratic phase.
+        bool stop = (a2 == 0.0 || o2 <= 1e-20 * a2) || (sweep >= 4 && prev >= 0.0 && o2 > 0.9 * prev);
+        prev = o2;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double* other = acc + 2 * ((sweep + 1) & 1);
+            other[0] = 0.0;
+            other[1] = 0.0;
+        }
+        if (stop) break;
+        grid.sync();
+    }
+    // whole sweeps bring every player back to its own seat: D is in the
+    // original column order
+    const float* Dc = Db[cur];
+    const long long tot = (long long)n * n;
+    for (long long e = gtid; e < tot; e += gstride) {
+        int r = (int)(e % n), c = (int)(e / n);
+        Dout[e] = Dc[r + (long long)c * npad];
+    }
+}
+
+cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, cudaStream_t st) {
+    int npad = ((n + 31) / 32) * 32;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine32_coop_kernel, 256, 0);
+    if (e != cudaSuccess) return e;
+    int T = npad / 32;
+    int grid = std::min(sms * std::max(1, std::min(per_sm, 4)), 2 * T * T);
+    void* args[] = {(void*)&B, (void*)&n, (void*)&npad, (void*)&ws, (void*)&Dout, (void*)&max_sweeps};
+    return cudaLaunchCooperativeKernel((const void*)refine32_coop_kernel, dim3(grid), dim3(256), args, 0, st);
+}
+
 size_t diag_fp32_ws_floats(int n) {
     long long npad = ((n + 31) / 32) * 32;
-    return (size_t)(4 * npad * npad + 64);
+    // refine32 also needs 2 npad doubles + 2 npad ints + 4 doubles
+    return (size_t)(4 * npad * npad + 6 * npad + 64);
 }
 
 // Q0 <- eigenvectors of fl32(A) (approximately).  ws: diag_fp32_ws_floats(n)

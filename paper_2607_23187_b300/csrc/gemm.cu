@@ -156,6 +156,36 @@ cudaError_t set_identity(double* dst, long long ldd, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// dst = fl64(fl32(src)): the matrix the FP32 decomposition describes
+__global__ void round_fp32_kernel(const double* s, long long lds, double* d, long long ldd, int n) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)n * n;
+    for (; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e % n), c = (int)(e / n);
+        d[r + c * ldd] = (double)__double2float_rn(s[r + c * lds]);
+    }
+}
+
+cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st) {
+    round_fp32_kernel<<<592, 256, 0, st>>>(src, lds, dst, ldd, n);
+    return cudaGetLastError();
+}
+
+// X <- X + Y
+__global__ void add_f64_kernel(double* X, long long ldx, const double* Y, long long ldy, int n) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)n * n;
+    for (; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e % n), c = (int)(e / n);
+        X[r + c * ldx] += Y[r + c * ldy];
+    }
+}
+
+cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st) {
+    add_f64_kernel<<<592, 256, 0, st>>>(X, ldx, Y, ldy, n);
+    return cudaGetLastError();
+}
+
 // Y <- 3I - Y
 __global__ void three_i_minus_kernel(double* Y, long long ldy, int n) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -84,11 +84,18 @@ cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cud
 cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
                             long long lda, const double* B, long long ldb, double beta, double* C,
                             long long ldc, void* ws, size_t ws_bytes, cudaStream_t st);
-size_t gemm_split_bf16_ws(int m, int n, int k);
+size_t gemm_split_bf16_ws(int m, int n, int k);          // 0: k too large for the exact split product
+int* gemm_split_bf16_errflag(void* ws);                 // device status word (0 = ok), sticky until cleared
+int gemm_split_bf16_launches(int m, int n, int k);      // kernel launches per product
+cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st);
 
 // diag32.cu: FP32 parallel-order Jacobi diagonalisation of fl32(A); Q0 out (ld n)
 cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
                       int max_sweeps, cudaStream_t st);
 size_t diag_fp32_ws_floats(int n);
+// refinement of an FP32 eigenbasis on B = X^T fl32(A) X; Dout: X (I + D)
+cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, cudaStream_t st);
+cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st);
+cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st);
 
 }  // namespace pjac

@@ -32,7 +32,7 @@ EXPORTS = (
     "pjac_solve", "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_default_opts",
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
-    "pjac_solve_preconditioned_noalloc",
+    "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
 )
 
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_solve.argtypes = [vp, vp, i, i, i, d, vp, vp, i, ctypes.POINTER(Info), vp]
         L.pjac_solve_preconditioned.argtypes = [vp, vp, i, i, vp, i, i, d, vp, vp, i,
                                                 ctypes.POINTER(Info), vp]
+        L.pjac_product.argtypes = [vp, i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]
         L.pjac_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, i, d, vp, vp]
         L.pjac_serve_default_opts.argtypes = [ctypes.POINTER(ServeOpts)]
         L.pjac_serve_default_opts.restype = None
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Info)]
         L.pjac_serve_progress.argtypes = [vp]
         L.pjac_serve_get_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+        L.pjac_solve_launch_count.argtypes = [vp, i]
         L.pjac_status_string.argtypes = [i]
         L.pjac_status_string.restype = ctypes.c_char_p
         L.pjac_last_error.argtypes = []
@@ -196,6 +198,31 @@ def pjac_precondition(h: Handle, a: torch.Tensor, q0: Optional[torch.Tensor] = N
     a1 = torch.empty((n, n), dtype=torch.float64, device=a.device)
     _check(load().pjac_precondition(h.h, _ptr(a), n, n, _ptr(q0c), _ptr(qt), n, _ptr(a1), n, _stream()))
     return qt.t(), a1
+
+
+def pjac_product(h: Handle, a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: bool = False,
+                 alpha: float = 1.0, beta: float = 0.0, c: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """alpha op(a) @ op(b) + beta c with the handle's transform (split-BF16
+    tensor-core product or plain FP64).  a, b: FP64 CUDA matrices (row-major
+    torch layout); op(x) = x.T when the flag is set.  The library works in
+    column-major order, so it is handed C^T = op(b)^T op(a)^T, which reads
+    the row-major storage of a and b directly."""
+    a = a.contiguous()
+    b = b.contiguous()
+    m = a.shape[1] if trans_a else a.shape[0]
+    k = a.shape[0] if trans_a else a.shape[1]
+    kb = b.shape[1] if trans_b else b.shape[0]
+    n = b.shape[0] if trans_b else b.shape[1]
+    if kb != k:
+        raise ValueError(f"inner dimensions differ: {k} vs {kb}")
+    if c is None:
+        c = torch.zeros((m, n), dtype=torch.float64, device=a.device)
+        beta = 0.0
+    elif c.shape != (m, n) or not c.is_contiguous():
+        raise ValueError("c must be a contiguous (m, n) tensor")
+    _check(load().pjac_product(h.h, 1 if trans_b else 0, 1 if trans_a else 0, n, m, k, float(alpha),
+                               _ptr(b), b.shape[1], _ptr(a), a.shape[1], float(beta), _ptr(c), n, _stream()))
+    return c
 
 
 def pjac_solve(h: Handle, a: torch.Tensor, pivot: str = "gap", tol: float = 1e-15,
