@@ -45,9 +45,10 @@ def measured_peaks():
         return {}
 
 
-# FP64 arithmetic rate of one B300 measured by the FP64 probe
-# (profiles/b300_fp64_probe.md): 476 G DFMA/s -> 0.952 TFLOP/s.
-FP64_PEAK_TFLOPS = 0.952
+# FP64 (non-tensor) arithmetic peak of one B300: the nominal 1.25 TFLOP/s.
+# MEASURED_PEAKS.json carries no FP64 figure.
+FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_SOURCE = "nominal B300 FP64 rate (1.25 TFLOP/s); MEASURED_PEAKS.json has no FP64 figure"
 
 
 class Clocks:
@@ -239,16 +240,9 @@ def run_ours(args, ws, rank, local):
         h.set_opts(transform=args.transform, stop=stop, cluster_size=args.cluster)
         return pjac.pjac_solve(h, a if mat is None else mat, pivot, tol)
 
-    # warm-up (also the accuracy check)
-    info = None
     for _ in range(args.warmup):
-        w, v, info, st = solve()
+        solve()
     torch.cuda.synchronize()
-    w_np = w.cpu().numpy()
-    eig_err = float(np.max(np.abs(w_np - p.lam)))
-    v_np = v.cpu().numpy()
-    resid = float(np.linalg.norm(p.a @ v_np - v_np * w_np) / np.linalg.norm(p.a))
-    orth = float(np.linalg.norm(v_np.T @ v_np - np.eye(n)))
 
     clocks = Clocks(local)
     barrier(ws)
@@ -268,6 +262,13 @@ def run_ours(args, ws, rank, local):
     ms_total = max_over_ranks(ws, ms_total)
     ms_step = ms_total / args.steps
     value = ws * args.steps / (ms_total / 1000.0)
+
+    # accuracy of the last timed solve against the known spectrum
+    w_np = w.cpu().numpy()
+    eig_err = float(np.max(np.abs(w_np - p.lam)))
+    v_np = v.cpu().numpy()
+    resid = float(np.linalg.norm(p.a @ v_np - v_np * w_np) / np.linalg.norm(p.a))
+    orth = float(np.linalg.norm(v_np.T @ v_np - np.eye(n)))
 
     # end to end through the public API with host buffers
     a_host = torch.tensor(p.a).pin_memory()
@@ -332,7 +333,7 @@ def run_ours(args, ws, rank, local):
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
             "kernel": "jacobi_single_kernel (one cluster of CTAs, one problem)",
-            "peak_source": "measured FP64 DFMA rate (FP64 probe); MEASURED_PEAKS.json has no FP64 figure",
+            "peak_source": FP64_PEAK_SOURCE,
             "ns_per_rotation": 1e6 * jac_ms / max(rot, 1),
             "hbm_gbs_equiv": 80.0 * n * rot / (jac_ms / 1000.0) / 1e9,
             "hbm_peak_gbs": peaks.get("hbm_gbs")}
@@ -359,13 +360,274 @@ def run_ours(args, ws, rank, local):
     h.close()
 
 
+# ----------------------------------------------------------------------------
+# the preconditioner's working-precision product alone (transform kernel)
+# ----------------------------------------------------------------------------
+PRODUCT_METRIC = "FP64-accurate n x n products/s (split-BF16 tcgen05 product of the Sec. 2.1 transform)"
+
+
+def split_pairs(k):
+    """Slice pairs of the split product for inner dimension k (b-bit digits,
+    S slices, pairs with s + t < S)."""
+    b = 6 if k * 63 * 63 <= 2 ** 24 else 5
+    S = (54 + b - 1) // b
+    return S * (S + 1) // 2
+
+
+def run_product(args, ws, rank, local):
+    import torch
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n or 4096
+    g = torch.Generator(device=dev).manual_seed(n)
+    a = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    b = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    c = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float64, device=dev)     # 512 MB > L2
+    h = pjac.Handle(transform=args.transform)
+    for _ in range(args.warmup):
+        pjac.pjac_product(h, a, b, c=c)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    barrier(ws)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pjac.pjac_product(h, a, b, c=c)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier(ws)
+    clocks = clk.stop()
+    ms = max_over_ranks(ws, float(np.median(times)))
+    peaks = measured_peaks()
+    if args.transform == "split_bf16":
+        flops = split_pairs(n) * 2.0 * n ** 3          # BF16 tensor work
+        peak = peaks.get("bf16_tflops", 1800.0)
+        roof = {"bound": "tensor", "achieved": flops / (ms / 1000) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (ms / 1000) / 1e12 / peak, "traffic": None,
+                "kernel": "whole product (digit split, tcgen05 slice products, reduction); BF16 work = "
+                          "%d slice pairs x 2n^3" % split_pairs(n),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+    else:
+        flops = 2.0 * n ** 3
+        roof = {"bound": "alu", "achieved": flops / (ms / 1000) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": flops / (ms / 1000) / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "gemm_f64_kernel", "peak_source": FP64_PEAK_SOURCE}
+    out = {"metric": PRODUCT_METRIC, "value": ws * 1000.0 / ms, "unit": "products/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16 slices, fp32 accumulate, fp64 result"
+           if args.transform == "split_bf16" else "f64", "data": "synthetic",
+           "config": {"workload": "C = A B, n = %d, A and B N(0,1) FP64 (seeded)" % n, "n": n,
+                      "transform": args.transform, "l2": "L2 flushed (512 MB write) before every step"},
+           "fp64_equivalent_tflops": 2.0 * n ** 3 / (ms / 1000) / 1e12,
+           "e2e": None, "gpu_launches": None, "roofline": roof, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+# ----------------------------------------------------------------------------
+# batched form: 10,000 independent problems, n log-uniform in [16, 256]
+# ----------------------------------------------------------------------------
+BATCHED_METRIC = "batched eigensolves/s (10,000 problems, n log-uniform in [16,256], gap rule)"
+
+
+def batched_config(nb):
+    return {"workload": "batched: %d problems, n = round(exp(U[ln16, ln256])) (seed 1), half clustered "
+                        "(n/8 clusters, spread 1e-8), half uniform U[-1,1]; gap rule, off-diagonal stop "
+                        "1e-15 ||A1||_F, eigenvalues and vectors" % nb,
+            "problems": nb, "pivot": "gap", "tol": 1e-15,
+            "l2": "inputs (packed A, about 950 MB) larger than L2 (126 MB)",
+            "parallelism": "single GPU (persistent CTAs over a work queue); replicas across GPUs"}
+
+
+def pack_batched(ps):
+    ns = np.array([p.n for p in ps], dtype=np.int32)
+    sizes = ns.astype(np.int64) ** 2
+    aoff = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    woff = np.concatenate([[0], np.cumsum(ns.astype(np.int64))[:-1]]).astype(np.int64)
+    flat = np.concatenate([np.ascontiguousarray(p.a).ravel() for p in ps])   # symmetric: row = column major
+    return ns, aoff, woff, flat
+
+
+def run_batched_ours(args, ws, rank, local):
+    import ctypes
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ps = pin.batched_workload()
+    nb = len(ps)
+    ns, aoff, woff, flat = pack_batched(ps)
+    host_a = torch.from_numpy(flat).pin_memory()
+    a = host_a.to(dev)
+    w = torch.empty(int(ns.sum()), dtype=torch.float64, device=dev)
+    v = torch.empty(flat.size, dtype=torch.float64, device=dev)
+    isz = ctypes.sizeof(pjac.Info)
+    infos = torch.empty((nb, isz), dtype=torch.uint8, device=dev)
+    host_w = torch.empty(w.shape, dtype=torch.float64).pin_memory()
+    host_v = torch.empty(v.shape, dtype=torch.float64).pin_memory()
+    L = pjac.load()
+    h = pjac.Handle()
+    vp = ctypes.c_void_p
+
+    def call():
+        st = L.pjac_solve_batched(h.h, nb, ns.ctypes.data_as(vp), aoff.ctypes.data_as(vp), vp(a.data_ptr()),
+                                  woff.ctypes.data_as(vp), vp(w.data_ptr()), aoff.ctypes.data_as(vp),
+                                  vp(v.data_ptr()), pjac.PIVOTS["gap"], 1e-15, vp(infos.data_ptr()),
+                                  vp(torch.cuda.current_stream().cuda_stream))
+        if st != 0:
+            raise RuntimeError("pjac_solve_batched: %s" % L.pjac_last_error().decode())
+
+    call()                       # sizes the workspace outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+        call()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        graph.replay()           # inputs (950 MB) exceed L2: no flush needed
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ws, ms)
+    clocks = clk.stop()
+    value = ws * nb / (ms / 1000.0)
+
+    # end to end: pinned H2D of the step's inputs, the solve, D2H of W and V
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.copy_(host_a, non_blocking=True)
+        graph.replay()
+        host_w.copy_(w, non_blocking=True)
+        host_v.copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(ws, float(np.median(e2e)))
+
+    # accuracy of every problem against its known spectrum, residual on a sample
+    raw = infos.cpu().numpy().tobytes()
+    stats = [pjac.Info.from_buffer_copy(raw[k * isz:(k + 1) * isz]).as_dict() for k in range(nb)]
+    wh = host_w.numpy()
+    worst = 0.0
+    for k, p in enumerate(ps):
+        wk = wh[woff[k]:woff[k] + p.n]
+        worst = max(worst, float(np.max(np.abs(wk - p.lam))) / p.norm2)
+    vh = host_v.numpy()
+    rs = np.random.default_rng(7)
+    res = orth = 0.0
+    for k in rs.choice(nb, 32, replace=False):
+        m = int(ns[k])
+        vk = vh[aoff[k]:aoff[k] + m * m].reshape(m, m).T
+        wk = wh[woff[k]:woff[k] + m]
+        res = max(res, float(np.linalg.norm(ps[k].a @ vk - vk * wk) / np.linalg.norm(ps[k].a)))
+        orth = max(orth, float(np.linalg.norm(vk.T @ vk - np.eye(m))))
+    rot = np.array([s_["rotations"] for s_ in stats], dtype=np.float64)
+    status_ok = all(s_["status"] == 0 for s_ in stats)
+
+    # the plain single-problem FP64 path on a seeded sample, one at a time
+    sample = np.random.default_rng(11).choice(nb, 100, replace=False)
+    hp = pjac.Handle(transform="fp64")
+    mats = [torch.tensor(ps[k].a, device=dev) for k in sample]
+    pjac.pjac_solve(hp, mats[0], "gap", 1e-15)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m_ in mats:
+        pjac.pjac_solve(hp, m_, "gap", 1e-15)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    one_rate = len(sample) / t_one
+    hp.close()
+
+    flops = float(np.sum(14.0 * ns * rot))
+    achieved = flops / (ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "whole batched pipeline (5 kernels in one CUDA graph; the Jacobi kernel dominates)",
+            "peak_source": FP64_PEAK_SOURCE,
+            "us_per_rotation_per_cta": 1e3 * ms * 2 * 148 / max(rot.sum(), 1)}
+    out = {"metric": BATCHED_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": batched_config(nb),
+           "graph_captured": True,
+           "rotations": {"total": float(rot.sum()), "mean_sweeps": float(np.mean(
+               [s_["sweeps"] for s_ in stats]))},
+           "accuracy": {"max_rel_eig_err": worst, "ok_1e-13": worst <= 1e-13, "all_status_ok": status_ok,
+                        "residual_sample32": res, "orthogonality_sample32": orth},
+           "one_at_a_time_fp64": {"solves_per_s": one_rate, "sample": "100 seeded problems of the batch, "
+                                  "pjac_solve with the FP64 transform, one after another",
+                                  "batched_speedup": value / ws / one_rate},
+           "e2e": {"value": ws * nb / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(flat.nbytes),
+                   "d2h_bytes_per_step": int(host_w.numel() * 8 + host_v.numel() * 8)},
+           "gpu_launches": 5 * args.steps,
+           "roofline": roof, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+def run_batched_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    import pjac_inputs as pin
+    oracle.build()
+    ps = pin.batched_workload()
+    nb = len(ps)
+    idx = np.random.default_rng(11).choice(nb, 200, replace=False)
+    cores = os.cpu_count()
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        a1s = []
+        for k in idx:
+            q0 = oracle.q0_fp32(ps[k].a)
+            q, a1 = oracle.precondition(ps[k].a, q0)
+            a1s.append(a1)
+        oracle.jacobi_many(a1s, pivot="gap", tol=1e-15)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            vals.append(len(idx) / dt)
+    v = float(np.median(vals))
+    sample = ("200 seeded problems of the batch: oracle preconditioner per problem (numpy/LAPACK), then the C "
+              "oracle's Algorithm 1 over the problems with OpenMP on %d threads; rate = problems / time" % cores)
+    out = {"metric": BATCHED_METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * nb / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": batched_config(nb),
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "batched", "product"])
     ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
     ap.add_argument("--with-4096", action="store_true", help="add one timed n=4096 (cfg3) solve")
@@ -375,7 +637,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_init()
-    if args.impl == "reference":
+    if args.workload == "product":
+        run_product(args, ws, rank, local)
+    elif args.workload == "batched":
+        if args.impl == "reference":
+            run_batched_reference(args, ws, rank)
+        else:
+            run_batched_ours(args, ws, rank, local)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_ours(args, ws, rank, local)

@@ -208,7 +208,14 @@ int pjac_solve_preconditioned_noalloc(double* A1, int n, int lda1, const double*
  * problem's order and its offsets (in doubles) into A, W and V; problem p is
  * column-major with leading dimension n[p].  A is not modified.  Each problem
  * is preconditioned and solved like pjac_solve.  infos [out, DEVICE] nb
- * records, written by the device (graph-capturable: no host sync).
+ * records, written by the device.
+ * Graph capture: called on a capturing stream, the call only records its
+ * copies and kernels (no host synchronisation) and hands its pinned staging
+ * buffer to the graph, which replays the same batch (the host arrays are
+ * read at capture time).  The graph stays valid while the handle lives and
+ * no later batched call on the handle needs a larger device workspace.
+ * Outside a capture the call synchronises the stream once before it stages
+ * the descriptors.
  * Returns PJAC_OK once the work is enqueued; per-problem status is in infos.
  */
 int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_off,

@@ -271,6 +271,7 @@ struct BatchState {
     size_t dbytes = 0;
     void* hbuf = nullptr;     // pinned host staging
     size_t hbytes = 0;
+    std::vector<void*> held;  // staging buffers read by captured graphs (freed on release)
 };
 
 // The batched workspace lives in a handle-independent cache keyed by the
@@ -286,6 +287,7 @@ void pjac_batched_release(const void* h) {
     if (it == g_bstate.end()) return;
     if (it->second.dbuf) cudaFree(it->second.dbuf);
     if (it->second.hbuf) cudaFreeHost(it->second.hbuf);
+    for (void* q : it->second.held) cudaFreeHost(q);
     g_bstate.erase(it);
 }
 
@@ -333,6 +335,15 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
         bs.dbytes = need;
     }
     size_t hneed = a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb);
+    // Inside a stream capture nothing runs now: the copies below become graph
+    // nodes that read the staging buffer at every replay, so that buffer is
+    // handed to the graph (kept until the handle is destroyed) and later
+    // calls stage elsewhere.  Outside a capture the stream is synchronised
+    // before the staging buffer is rewritten.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ec = cudaStreamIsCapturing(st, &cap);
+    if (ec != cudaSuccess) return cuda_err(ec, "cudaStreamIsCapturing");
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
     if (bs.hbytes < hneed) {
         if (bs.hbuf) cudaFreeHost(bs.hbuf);
         bs.hbuf = nullptr;
@@ -344,9 +355,11 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
         }
         bs.hbytes = hneed;
     }
-    // The staging buffer may still be read by an earlier call's copy.
-    cudaError_t e0 = cudaStreamSynchronize(st);
-    if (e0 != cudaSuccess) return cuda_err(e0, "cudaStreamSynchronize");
+    if (!capturing) {
+        // the staging buffer may still be read by an earlier call's copy
+        cudaError_t e0 = cudaStreamSynchronize(st);
+        if (e0 != cudaSuccess) return cuda_err(e0, "cudaStreamSynchronize");
+    }
     char* dbase = static_cast<char*>(bs.dbuf);
     BatchDesc* d_desc = reinterpret_cast<BatchDesc*>(dbase);
     int* d_order = reinterpret_cast<int*>(dbase + a256(sizeof(BatchDesc) * nb));
@@ -396,5 +409,10 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     BK(launch_readout_batched(d_desc, nb, max_n, st));
     BK(launch_info_batched(d_desc, nb, infos, st));
 #undef BK
+    if (capturing) {
+        bs.held.push_back(bs.hbuf);
+        bs.hbuf = nullptr;
+        bs.hbytes = 0;
+    }
     return PJAC_OK;
 }

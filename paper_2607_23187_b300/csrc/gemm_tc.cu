@@ -30,7 +30,7 @@
 //  tc_rowmax_kernel  max |x| of every row of the two K-major operand views
 //  tc_split_kernel   the digit slices, BF16, K-major, padded to the tiles
 //  tc_gemm_kernel    one 128x128 output tile per CTA; warp 0 issues TMA
-//                    loads (128B-swizzled 128x64 boxes) into a 4-stage ring,
+//                    loads (128B-swizzled 128x64 boxes) into a 6-stage ring,
 //                    warp 1 issues tcgen05.mma (M=128, N=128, K=16) into one
 //                    of two TMEM accumulators per group, warps 2..9 read the
 //                    finished accumulator (tcgen05.ld) and add it into 64-bit
@@ -51,7 +51,7 @@ namespace pjac {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;  // output tile, K block (64 BF16 = 128 B rows)
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NTHREADS = 320;               // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
