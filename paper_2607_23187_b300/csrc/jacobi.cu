@@ -7,12 +7,25 @@
 // (i,j) it
 //   1. rotates the entries (k,i),(k,j) and their mirrors (i,k),(j,k) for
 //      k in K_c, and the entries (k,i),(k,j) of V,
-//   2. scores the new entries: its own rows k compare their cached best
-//      entry with (k,i),(k,j) (rows whose best sat in column i or j are
-//      rescanned), and the new rows i and j are scored over K_c,
+//   2. scores the new entries: its own rows k update their cached entries
+//      with (k,i),(k,j) (see the row cache below), and the new rows i and j
+//      are scored over K_c,
 //   3. publishes three candidates (its best own row, its part of row i, its
-//      part of row j) in shared memory; one cluster barrier later every CTA
-//      reads all P slots through DSMEM and makes the same selection.
+//      part of row j) and the two largest keys of its parts of rows i and j
+//      in shared memory; one cluster barrier later every CTA reads all P
+//      slots and makes the same selection.
+//
+// Row cache (Sec. 3.2's O(n) update, with fewer rescans): each owned row k
+// keeps a list of up to two of its entries in exact score order and a key
+// bound F_k: every entry of the row outside the list has a key <= F_k.  When
+// (k,i),(k,j) change, list entries in those columns are dropped and the new
+// entries are inserted if their keys exceed F_k (an entry pushed out of the
+// list raises F_k to its own key).  The list head is the exact row maximum
+// as long as it was not dropped; a new head is certified when its key
+// exceeds F_k by the tie band.  Only an empty or uncertified list triggers a
+// rescan.  Rows i and j get their new head from the cluster exchange, and
+// as F the largest key among their other entries (from the two largest keys
+// of every CTA's part).
 // Scores are ranked by integer keys; entries whose keys are within the tie
 // band are compared on their exact FP64 scores, so the pivot is the exact
 // argmax of the FP64 scores with ties to the smallest (i,j).
@@ -31,7 +44,7 @@ namespace cg = cooperative_groups;
 namespace pjac {
 
 constexpr int NT = 256;     // threads per CTA
-constexpr int MAXR = 4;     // owned indices per thread (m <= NT * MAXR)
+constexpr int MAXR = 4;     // owned indices per thread (m <= NT * MAXR); MR <= MAXR per kernel
 
 struct Cand {
     int key, row, col, pad;
@@ -41,6 +54,7 @@ struct Cand {
 
 struct Slot {
     Cand loc, pi, pj;       // this CTA's best own row, its part of row i, of row j
+    int ki[2], kj[2];       // the two largest keys of its parts of rows i and j
     double prm[3][3];       // (c, s, t) of the rotation of each of the three
     double sum;
     int flags, pad;
@@ -49,7 +63,10 @@ struct Slot {
 struct Sh {
     int wk3[NT / 32][3];
     int wn3[NT / 32][3];
+    int wp3[NT / 32][3][2]; // per warp: smallest and largest pair id among contenders
     Cand out3[3];
+    int fij[2];             // key bounds F of the new rows i and j
+    int wkk[NT / 32][4];    // per-warp two largest keys of rows i and j
     int wkey[NT / 32];
     Cand wc[NT / 32];
     double wsum[NT / 32];
@@ -67,7 +84,7 @@ struct Sh {
 
 #ifdef PJAC_PROFILE
 // Profiling build only: per-phase clock totals of CTA 0 and event counts.
-__device__ unsigned long long g_prof[24];
+__device__ unsigned long long g_prof[40];
 #define PROF_ADD(k, v) atomicAdd(&g_prof[k], (unsigned long long)(v))
 // exact evaluations made by this CTA (one counter per CTA)
 __device__ __forceinline__ unsigned int& prof_exact() {
@@ -139,6 +156,77 @@ __device__ __forceinline__ int block_max_int(int v, Sh& sh) {
     for (int k = 1; k < NT / 32; ++k) r = max(r, sh.wkey[k]);
     __syncthreads();
     return r;
+}
+
+// ---- row cache: a list of up to two entries and a key bound F ----------
+// Key bound for the entries below an exactly known one (every entry with an
+// FP64 score <= b's has a key <= the result): the key itself for the greedy
+// rule (monotone), b's key plus the key error margin for the gap rule (keys
+// below KEY_SUB are bounded by KEY_SUB + margin), KEY_NONE when there is no
+// such entry.
+__device__ __forceinline__ int bound_from_exact(const Cand& b, int pivot) {
+    if (b.key == KEY_NONE) return KEY_NONE;
+    if (pivot == PJAC_PIVOT_GREEDY) return b.key;
+    if (b.key == KEY_ZERO) return KEY_ZERO;
+    return max(b.key, KEY_SUB) + KEY_GAP_TIE;
+}
+
+// Insert entry e into the list (cur, sec) whose outside entries have keys
+// <= F; an entry that leaves the list raises F to its key.  e is always
+// compared with the head exactly, so a head that was the row's maximum stays
+// it; below the head, an entry whose key is <= F may stay outside.
+__device__ __forceinline__ void list_insert(Cand& e, Cand& cur, Cand& sec, int& F, int pivot,
+                                            const double* diag) {
+    if (e.key == KEY_NONE) return;
+    if (cur.key == KEY_NONE) {
+        if (F != KEY_NONE && e.key <= F) return;
+        cur = e;
+        return;
+    }
+    if (better(e, cur, pivot, diag)) {
+        if (sec.key != KEY_NONE) F = (F == KEY_NONE) ? sec.key : max(F, sec.key);
+        sec = cur;
+        cur = e;
+        return;
+    }
+    if (F != KEY_NONE && e.key <= F) return;     // stays outside, under the bound
+    if (sec.key == KEY_NONE) { sec = e; return; }
+    if (better(e, sec, pivot, diag)) {
+        F = (F == KEY_NONE) ? sec.key : max(F, sec.key);
+        sec = e;
+        return;
+    }
+    F = (F == KEY_NONE) ? e.key : max(F, e.key);
+}
+
+// Two largest keys (with multiplicity) of a set, as a pair k1 >= k2.
+__device__ __forceinline__ void key_push(int k, int& k1, int& k2) {
+    if (k > k1) { k2 = k1; k1 = k; }
+    else if (k > k2) k2 = k;
+}
+// Warp-wide two largest keys from per-lane pairs (every lane gets them).
+__device__ __forceinline__ void warp_top2_keys(int& k1, int& k2) {
+    const int m1 = __reduce_max_sync(0xffffffffu, k1);
+    const unsigned at = __ballot_sync(0xffffffffu, k1 == m1);
+    const int m2 = __reduce_max_sync(0xffffffffu, k1 == m1 ? k2 : k1);
+    k1 = m1;
+    k2 = (__popc(at) > 1) ? m1 : m2;
+}
+// Key bound F of a row whose head is h, given the two largest keys of all
+// its entries: the largest key of the entries other than h.
+__device__ __forceinline__ int bound_without_head(const Cand& h, int k1, int k2) {
+    return (h.key == k1) ? k2 : k1;
+}
+
+// Is the list head cur certainly the row's exact maximum, given only that
+// the entries outside the list have keys <= F?
+__device__ __forceinline__ bool head_certified(const Cand& cur, int F, int pivot) {
+    if (cur.key == KEY_NONE) return false;
+    if (F == KEY_NONE) return true;
+    if (pivot == PJAC_PIVOT_GREEDY) return cur.key > F;
+    if (cur.key == KEY_ZERO) return F <= KEY_ZERO;   // the row's maximum is 0
+    if (cur.key < KEY_SUB) return false;              // keys do not decide there
+    return (long long)cur.key > (long long)F + KEY_GAP_TIE;
 }
 
 __device__ __forceinline__ Cand shfl_cand(const Cand& c, int src) {
@@ -251,14 +339,32 @@ __device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag
 // per thread) in one pass: one barrier for the three maximum keys, one for
 // the contender counts, one for the results; the exact phase runs only for
 // a kind with several contenders.  Uniform call.
-__device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh) {
+__device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh,
+                              int (&kA)[2], int (&kB)[2]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tie = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_GAP_TIE;
     int w0 = __reduce_max_sync(0xffffffffu, c0.key);
     int w1 = __reduce_max_sync(0xffffffffu, c1.key);
     int w2 = __reduce_max_sync(0xffffffffu, c2.key);
-    if (lane == 0) { sh.wk3[warp][0] = w0; sh.wk3[warp][1] = w1; sh.wk3[warp][2] = w2; }
+    warp_top2_keys(kA[0], kA[1]);
+    warp_top2_keys(kB[0], kB[1]);
+    if (lane == 0) {
+        sh.wk3[warp][0] = w0; sh.wk3[warp][1] = w1; sh.wk3[warp][2] = w2;
+        sh.wkk[warp][0] = kA[0]; sh.wkk[warp][1] = kA[1]; sh.wkk[warp][2] = kB[0]; sh.wkk[warp][3] = kB[1];
+    }
     __syncthreads();
+    // the two largest keys of kA and kB over the block (every thread)
+    {
+        int a1 = KEY_NONE, a2 = KEY_NONE, b1 = KEY_NONE, b2 = KEY_NONE;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            key_push(sh.wkk[w][0], a1, a2);
+            key_push(sh.wkk[w][1], a1, a2);
+            key_push(sh.wkk[w][2], b1, b2);
+            key_push(sh.wkk[w][3], b1, b2);
+        }
+        kA[0] = a1; kA[1] = a2; kB[0] = b1; kB[1] = b2;
+    }
     int m[3] = {sh.wk3[0][0], sh.wk3[0][1], sh.wk3[0][2]};
 #pragma unroll
     for (int w = 1; w < NT / 32; ++w) {
@@ -274,25 +380,43 @@ __device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const dou
         t[q] = m[q] != KEY_NONE && cs[q].key != KEY_NONE &&
                (exact_all || (long long)cs[q].key >= (long long)m[q] - tie);
         unsigned b = __ballot_sync(0xffffffffu, t[q]);
-        if (lane == 0) sh.wn3[warp][q] = __popc(b);
+        // unordered pair id (indices < 2^15) of the contenders
+        const int pid = t[q] ? ((min(cs[q].row, cs[q].col) << 15) | max(cs[q].row, cs[q].col)) : INT_MAX;
+        const int pmin = __reduce_min_sync(0xffffffffu, pid);
+        const int pmax = __reduce_max_sync(0xffffffffu, t[q] ? pid : -1);
+        if (lane == 0) {
+            sh.wn3[warp][q] = __popc(b);
+            sh.wp3[warp][q][0] = pmin;
+            sh.wp3[warp][q][1] = pmax;
+        }
     }
     __syncthreads();
     int cnt[3] = {0, 0, 0};
+    bool one_pair[3];
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        cnt[0] += sh.wn3[w][0];
-        cnt[1] += sh.wn3[w][1];
-        cnt[2] += sh.wn3[w][2];
+    for (int q = 0; q < 3; ++q) {
+        int gmin = INT_MAX, gmax = -1;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) {
+            cnt[q] += sh.wn3[w][q];
+            gmin = min(gmin, sh.wp3[w][q][0]);
+            gmax = max(gmax, sh.wp3[w][q][1]);
+        }
+        // several contenders that are all the same pair seen from its two
+        // rows: equal scores, the row with row < col wins (as in better())
+        one_pair[q] = cnt[q] > 1 && gmin == gmax;
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 3; ++q) {
         if (cnt[q] == 1 && t[q]) sh.out3[q] = cs[q];
+        if (one_pair[q] && t[q] && cs[q].row < cs[q].col) sh.out3[q] = cs[q];
+    }
     __syncthreads();
     Cand r[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        r[q] = (cnt[q] == 1) ? sh.out3[q] : no_cand();
-        if (cnt[q] > 1) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh);
+        r[q] = (cnt[q] == 1 || one_pair[q]) ? sh.out3[q] : no_cand();
+        if (cnt[q] > 1 && !one_pair[q]) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh);
     }
     c0 = r[0];
     c1 = r[1];
@@ -369,13 +493,12 @@ __device__ __forceinline__ const Slot* peer_slot(Sh& sh, int par, int r) {
     return &sh.slots[par];
 }
 
-// Rescan row k (block-wide): best entry over l != k.
-// Rescan row k (block-wide): its best entry over l != k, and in sec the
-// best entry in any other column (the top two of the row).
-__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& sec) {
+// Rescan row k (block-wide): its best entry over l != k, in sec its second
+// entry, and in F the key bound of its remaining entries (from its third).
+__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& sec, int& F) {
     const double* row = a.A + (long long)k * a.lda;
     double dk = diag[k];
-    Cand t1 = no_cand(), t2 = no_cand();
+    Cand t1 = no_cand(), t2 = no_cand(), t3 = no_cand();
     for (int l0 = threadIdx.x; l0 < a.n; l0 += 4 * NT) {
         double xs[4];
 #pragma unroll
@@ -390,13 +513,21 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, 
             Cand c;
             c.row = k; c.col = l; c.pad = 0; c.x = xs[u]; c.ex = -1.0;
             c.key = entry_key(a.pivot, xs[u], a.pivot == PJAC_PIVOT_GREEDY ? 0.0 : __dadd_rn(dk, -diag[l]));
-            if (better(c, t1, a.pivot, diag)) { t2 = t1; t1 = c; }
-            else if (better(c, t2, a.pivot, diag)) t2 = c;
+            if (better(c, t1, a.pivot, diag)) { t3 = t2; t2 = t1; t1 = c; }
+            else if (better(c, t2, a.pivot, diag)) { t3 = t2; t2 = c; }
+            else if (better(c, t3, a.pivot, diag)) t3 = c;
         }
     }
     Cand b = block_select(t1, a.pivot, diag, sh);
-    Cand offer = (t1.key != KEY_NONE && t1.col == b.col) ? t2 : t1;
+    const bool w1 = t1.key != KEY_NONE && t1.col == b.col;
+    Cand offer = w1 ? t2 : t1;
     sec = block_select(offer, a.pivot, diag, sh);
+    // the thread's best entry that is neither b nor sec
+    Cand o3 = t1;
+    if (o3.key != KEY_NONE && (o3.col == b.col || o3.col == sec.col)) o3 = t2;
+    if (o3.key != KEY_NONE && (o3.col == b.col || o3.col == sec.col)) o3 = t3;
+    Cand third = block_select(o3, a.pivot, diag, sh);
+    F = bound_from_exact(third, a.pivot);
     return b;
 }
 
@@ -415,12 +546,13 @@ __device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, S
 }
 
 // Solve one problem.  rank/P: this CTA's rank in the cluster and the
-// cluster size.  Shared arrays: diag[n], cache[m] (best entry of each owned
-// row), cache2[m] (best entry in another column, or none when unknown),
+// cluster size.  Shared arrays: diag[n]; per owned row: cache[m] (the list
+// head, the row's exact best entry), cache2[m] (the list's second entry or
+// none), cachef[m] (the key bound F of the entries outside the list);
 // resc[m].
-template <bool CLUSTER>
+template <bool CLUSTER, int MR>
 __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double* diag,
-                               Cand* cache, Cand* cache2, int* resc) {
+                               Cand* cache, Cand* cache2, int* cachef, int* resc) {
     const int n = a.n;
     const int tid = threadIdx.x;
     const int mchunk = (n + P - 1) / P;
@@ -435,8 +567,11 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     __syncthreads();
 #define LAP(k) do { if (rank == 0 && tid == 0) { long long nw = clock64(); PROF_ADD(k, nw - pt); pt = nw; \
         unsigned int ce = prof_exact(); PROF_ADD(12 + (k), ce - pex); pex = ce; } } while (0)
+// time since the last LAP, without starting a new phase
+#define SLAP(k) do { if (rank == 0 && tid == 0) PROF_ADD(24 + (k), clock64() - pt); } while (0)
 #else
 #define LAP(k) ((void)0)
+#define SLAP(k) ((void)0)
 #endif
 
     for (int k = tid; k < n; k += NT) diag[k] = ldcg(a.A + (long long)k * a.lda + k);
@@ -515,12 +650,12 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     // ---- rotate rows/cols i,j for the owned indices, and V ----
     // Loads of the entries a rotation (i,j) changes, issued before the
     // rotation parameters are known (they depend only on i, j).
-    double px[MAXR], py[MAXR], pvx[MAXR], pvy[MAXR];
+    double px[MR], py[MR], pvx[MR], pvy[MR];
     auto preload = [&](int i, int j) {
         const double* Ai = a.A + (long long)i * a.lda;
         const double* Aj = a.A + (long long)j * a.lda;
 #pragma unroll
-        for (int r = 0; r < MAXR; ++r) {
+        for (int r = 0; r < MR; ++r) {
             int k = k0 + tid + r * NT;
             px[r] = py[r] = pvx[r] = pvy[r] = 0.0;
             if (k < k1) {
@@ -534,14 +669,16 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         }
     };
 
+    // pI (pJ): this thread's best entry of the new row i (row j) over its
+    // owned columns; kI (kJ): the two largest keys among them.
     auto rotate_owned = [&](int i, int j, const double c, const double s, const double dii_new,
-                            const double djj_new, bool score, Cand& pI, Cand& pJ) {
+                            const double djj_new, bool score, Cand& pI, Cand& pJ, int (&kI)[2], int (&kJ)[2]) {
         double* Ai = a.A + (long long)i * a.lda;
         double* Aj = a.A + (long long)j * a.lda;
         const int cmin = min(i, j), cmax = max(i, j);
         const double di = diag[i], dj = diag[j];   // already updated
 #pragma unroll
-        for (int r = 0; r < MAXR; ++r) {
+        for (int r = 0; r < MR; ++r) {
             int k = k0 + tid + r * NT;
             if (k >= k1) break;
             if (a.V) {
@@ -559,6 +696,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     Cand z; z.key = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO; z.row = j; z.col = i;
                     z.pad = 0; z.x = 0.0; z.ex = -1.0;
                     if (better(z, pJ, pivot, diag)) pJ = z;
+                    key_push(z.key, kJ[0], kJ[1]);
                 }
                 continue;
             }
@@ -570,6 +708,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     Cand z; z.key = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO; z.row = i; z.col = j;
                     z.pad = 0; z.x = 0.0; z.ex = -1.0;
                     if (better(z, pI, pivot, diag)) pI = z;
+                    key_push(z.key, kI[0], kI[1]);
                 }
                 continue;
             }
@@ -582,6 +721,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             stcg(Ak + i, xn);
             stcg(Ak + j, yn);
             if (!score) continue;
+            if (r == 0) SLAP(5);
             double dk = diag[k];
             int kx, ky;
             if (pivot == PJAC_PIVOT_GREEDY) {
@@ -591,13 +731,14 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 kx = gap_key(xn, __dadd_rn(dk, -di));
                 ky = gap_key(yn, __dadd_rn(dk, -dj));
             }
+            if (r == 0) SLAP(6);
             Cand ci; ci.key = kx; ci.row = i; ci.col = k; ci.pad = 0; ci.x = xn; ci.ex = -1.0;
             Cand cj; cj.key = ky; cj.row = j; cj.col = k; cj.pad = 0; cj.x = yn; cj.ex = -1.0;
             if (better(ci, pI, pivot, diag)) pI = ci;
             if (better(cj, pJ, pivot, diag)) pJ = cj;
-            // own row k: only its entries (k,i), (k,j) changed.  Keep its best
-            // entry and, when known, its best entry in another column;
-            // rescan only when neither survives.
+            key_push(kx, kI[0], kI[1]);
+            key_push(ky, kJ[0], kJ[1]);
+            // own row k: only its entries (k,i), (k,j) changed
             Cand e1, e2;
             e1.row = k; e1.pad = 0; e1.ex = -1.0;
             e2 = e1;
@@ -606,49 +747,25 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             (void)cmax;
             Cand cur = cache[k - k0];
             Cand sec = cache2[k - k0];
+            int F = cachef[k - k0];
             if (sec.key != KEY_NONE && (sec.col == i || sec.col == j)) sec = no_cand();
-            if (cur.col == i || cur.col == j) {
-                if (sec.key == KEY_NONE) {
-                    int slot = atomicAdd(&sh.nresc, 1);
-                    resc[slot] = k;
-                } else {
-                    // every untouched entry is <= sec
-                    Cand nb = sec;
-                    int w = 0;
-                    if (better(e1, nb, pivot, diag)) { nb = e1; w = 1; }
-                    if (better(e2, nb, pivot, diag)) { nb = e2; w = 2; }
-                    if (w == 0) {
-                        cur = sec;
-                        sec = no_cand();
-                    } else {
-                        Cand other = (w == 1) ? e2 : e1;
-                        cur = nb;
-                        if (better(other, sec, pivot, diag)) sec = other;
-                    }
-                    cache[k - k0] = cur;
-                    cache2[k - k0] = sec;
-                }
+            bool lost = false;
+            if (cur.key != KEY_NONE && (cur.col == i || cur.col == j)) {
+                cur = sec;
+                sec = no_cand();
+                lost = true;
+            }
+            list_insert(e1, cur, sec, F, pivot, diag);
+            list_insert(e2, cur, sec, F, pivot, diag);
+            if (cur.key == KEY_NONE || (lost && !head_certified(cur, F, pivot))) {
+                int slot = atomicAdd(&sh.nresc, 1);
+                resc[slot] = k;
             } else {
-                Cand nb = cur;
-                int w = 0;
-                if (better(e1, nb, pivot, diag)) { nb = e1; w = 1; }
-                if (better(e2, nb, pivot, diag)) { nb = e2; w = 2; }
-                if (w == 0) {
-                    if (sec.key != KEY_NONE) {
-                        if (better(e1, sec, pivot, diag)) sec = e1;
-                        if (better(e2, sec, pivot, diag)) sec = e2;
-                    }
-                } else {
-                    // the old best bounds every untouched entry
-                    Cand other = (w == 1) ? e2 : e1;
-                    Cand ns = cur;
-                    if (better(other, ns, pivot, diag)) ns = other;
-                    cur = nb;
-                    sec = ns;
-                }
                 cache[k - k0] = cur;
                 cache2[k - k0] = sec;
+                cachef[k - k0] = F;
             }
+            if (r == 0) SLAP(7);
         }
     };
 
@@ -677,8 +794,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     if (tid == 0) { diag[i] = dii; diag[j] = djj; }
                     __syncthreads();
                     Cand d1 = no_cand(), d2 = no_cand();
+                    int dk1[2] = {KEY_NONE, KEY_NONE}, dk2[2] = {KEY_NONE, KEY_NONE};
                     preload(i, j);
-                    rotate_owned(i, j, c, s, dii, djj, false, d1, d2);
+                    rotate_owned(i, j, c, s, dii, djj, false, d1, d2, dk1, dk2);
                     rot++;
                     any = true;
                     cta_exchange_sync<CLUSTER>();
@@ -692,8 +810,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         // initial scan (Sec. 3.2: O(n^2) scores once)
         for (int k = k0; k < k1; ++k) {
             Cand s2;
-            Cand b = rescan_row(a, k, diag, sh, s2);
-            if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; }
+            int F;
+            Cand b = rescan_row(a, k, diag, sh, s2, F);
+            if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; cachef[k - k0] = F; }
         }
         __syncthreads();
         // Publish this CTA's three candidates (best own row, its part of row
@@ -703,7 +822,8 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         // barrier.  Every CTA ends with the same winner in sh.sel and its
         // rotation in sh.c, sh.s, sh.t; the owners of rows i and j take
         // those rows' new bests.  i, j < 0: no rows i, j (first selection).
-        auto publish_select = [&](Cand loc, Cand pI, Cand pJ, int i, int j) {
+        auto publish_select = [&](Cand loc, Cand pI, Cand pJ, const int (&kI)[2], const int (&kJ)[2], int i,
+                                  int j) {
             if (tid < 3) {
                 Cand c = (tid == 0) ? loc : (tid == 1 ? pI : pJ);
                 double pc = 1.0, ps = 0.0, pt = 0.0;
@@ -721,8 +841,13 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 sh.stage.prm[tid][0] = pc;
                 sh.stage.prm[tid][1] = ps;
                 sh.stage.prm[tid][2] = pt;
-                if (tid == 0) { sh.stage.sum = 0.0; sh.stage.flags = sh.tflag; sh.stage.pad = 0; }
+                if (tid == 0) {
+                    sh.stage.sum = 0.0; sh.stage.flags = sh.tflag; sh.stage.pad = 0;
+                    sh.stage.ki[0] = kI[0]; sh.stage.ki[1] = kI[1];
+                    sh.stage.kj[0] = kJ[0]; sh.stage.kj[1] = kJ[1];
+                }
             }
+            SLAP(0);
             __syncwarp();
             if (tid < P) {
                 if (CLUSTER) {
@@ -732,6 +857,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     sh.inbox[par][0] = sh.stage;
                 }
             }
+            SLAP(1);
             cta_exchange_sync<CLUSTER>();
             LAP(5);
             const int warp = tid >> 5, lane = tid & 31;
@@ -746,14 +872,34 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 }
                 c = warp_best(c, width, pivot, diag);
                 if (lane == 0) sh.out3[warp] = c;
+                if (warp > 0) {
+                    // F of the new row i (row j): largest key of its entries
+                    // other than the head, from every rank's two largest keys
+                    int k1 = KEY_NONE, k2 = KEY_NONE;
+                    if (lane < P) {
+                        const Slot& sl = sh.inbox[par][lane];
+                        k1 = (warp == 1) ? sl.ki[0] : sl.kj[0];
+                        k2 = (warp == 1) ? sl.ki[1] : sl.kj[1];
+                    }
+                    warp_top2_keys(k1, k2);
+                    if (lane == 0) sh.fij[warp - 1] = bound_without_head(c, k1, k2);
+                }
             }
             __syncthreads();
             if (tid == 0) {
                 Cand g = sh.out3[0], bi = sh.out3[1], bj = sh.out3[2];
                 if (better(bi, g, pivot, diag)) g = bi;
                 if (better(bj, g, pivot, diag)) g = bj;
-                if (i >= k0 && i < k1) { cache[i - k0] = bi; cache2[i - k0] = no_cand(); }
-                if (j >= k0 && j < k1) { cache[j - k0] = bj; cache2[j - k0] = no_cand(); }
+                if (i >= k0 && i < k1) {
+                    cache[i - k0] = bi;
+                    cache2[i - k0] = no_cand();
+                    cachef[i - k0] = sh.fij[0];
+                }
+                if (j >= k0 && j < k1) {
+                    cache[j - k0] = bj;
+                    cache2[j - k0] = no_cand();
+                    cachef[j - k0] = sh.fij[1];
+                }
                 if (g.key != KEY_NONE) {
                     const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
                     sh.c = pr[0];
@@ -771,7 +917,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         {
             Cand loc = no_cand();
 #pragma unroll
-            for (int r = 0; r < MAXR; ++r) {
+            for (int r = 0; r < MR; ++r) {
                 int k = k0 + tid + r * NT;
                 if (k >= k1) break;
                 Cand c = cache[k - k0];
@@ -779,7 +925,8 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             }
             if (tid == 0) sh.tflag = 0;
             loc = block_select(loc, pivot, diag, sh);
-            publish_select(loc, no_cand(), no_cand(), -1, -1);
+            const int kn[2] = {KEY_NONE, KEY_NONE};
+            publish_select(loc, no_cand(), no_cand(), kn, kn, -1, -1);
         }
         bool stop_now = false;
         for (;;) {
@@ -793,6 +940,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 Cand g0 = sh.sel;
                 if (g0.key != KEY_NONE) preload(min(g0.row, g0.col), max(g0.row, g0.col));
             }
+            SLAP(3);
             // decisions on the current selection (thread 0, then broadcast);
             // its exact score and rotation arrived with it
             if (tid == 0) {
@@ -830,7 +978,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             const int i = sh.pi, j = sh.pj;
             const double c = sh.c, s = sh.s, dii = sh.dii, djj = sh.djj;
             Cand pI = no_cand(), pJ = no_cand();
-            rotate_owned(i, j, c, s, dii, djj, true, pI, pJ);
+            int kI[2] = {KEY_NONE, KEY_NONE}, kJ[2] = {KEY_NONE, KEY_NONE};
+            rotate_owned(i, j, c, s, dii, djj, true, pI, pJ, kI, kJ);
+            SLAP(4);
             rot++;
             __syncthreads();
             LAP(2);
@@ -840,8 +990,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             for (int r = 0; r < nr; ++r) {
                 int k = resc[r];
                 Cand s2;
-                Cand b = rescan_row(a, k, diag, sh, s2);
-                if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; }
+                int F;
+                Cand b = rescan_row(a, k, diag, sh, s2, F);
+                if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; cachef[k - k0] = F; }
             }
             __syncthreads();
             LAP(3);
@@ -849,20 +1000,22 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 sh.tflag = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
             Cand loc = no_cand();
 #pragma unroll
-            for (int r = 0; r < MAXR; ++r) {
+            for (int r = 0; r < MR; ++r) {
                 int k = k0 + tid + r * NT;
                 if (k >= k1) break;
                 if (k == i || k == j) continue;
                 Cand cc = cache[k - k0];
                 if (better(cc, loc, pivot, diag)) loc = cc;
             }
-            block_select3(loc, pI, pJ, pivot, diag, sh);
+            SLAP(2);
+            block_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ);
             LAP(4);
-            publish_select(loc, pI, pJ, i, j);
+            publish_select(loc, pI, pJ, kI, kJ, i, j);
             LAP(6);
             if (sh.decision == 2) { status = PJAC_ETIMEOUT; break; }
         }
 #undef LAP
+#undef SLAP
         if (rank == 0 && tid == 0) PROF_ADD(10, rot);
         if (tid == 0) last_score = sh.sel.key == KEY_NONE ? 0.0 :
                           (pivot == PJAC_PIVOT_GREEDY ? fabs(sh.sel.x) : cand_value(sh.sel, pivot, diag));
@@ -895,7 +1048,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
 
 size_t jacobi_smem_bytes(int n, int P) {
     int m = (n + P - 1) / P;
-    return (size_t)n * sizeof(double) + 2 * (size_t)m * sizeof(Cand) + (size_t)m * sizeof(int) + 16;
+    return (size_t)n * sizeof(double) + 2 * (size_t)m * sizeof(Cand) + 2 * (size_t)m * sizeof(int) + 16;
 }
 
 template <bool CLUSTER>
@@ -912,12 +1065,16 @@ __global__ void __launch_bounds__(NT, 1) jacobi_single_kernel(JacArgs a) {
     double* diag = reinterpret_cast<double*>(dyn);
     Cand* cache = reinterpret_cast<Cand*>(diag + a.n);
     Cand* cache2 = cache + m;
-    int* resc = reinterpret_cast<int*>(cache2 + m);
-    jacobi_problem<CLUSTER>(a, rank, P, sh, diag, cache, cache2, resc);
+    int* cachef = reinterpret_cast<int*>(cache2 + m);
+    int* resc = cachef + m;
+    jacobi_problem<CLUSTER, MAXR>(a, rank, P, sh, diag, cache, cache2, cachef, resc);
 }
 
-// Batched form: each CTA takes problems from a queue (largest first).
-__global__ void __launch_bounds__(NT) jacobi_batched_kernel(const BatchDesc* desc, int nb,
+// Batched form: each CTA takes problems from a queue (largest first).  MR
+// owned indices per thread: 1 when every order is <= NT (fewer registers,
+// two CTAs per SM), else MAXR.
+template <int MR>
+__global__ void __launch_bounds__(NT, MR == 1 ? 2 : 1) jacobi_batched_kernel(const BatchDesc* desc, int nb,
                                                            const int* order, int* counter,
                                                            int pivot, int stop, double tol,
                                                            long long max_rot_per_n2,
@@ -940,8 +1097,9 @@ __global__ void __launch_bounds__(NT) jacobi_batched_kernel(const BatchDesc* des
         double* diag = reinterpret_cast<double*>(dyn);
         Cand* cache = reinterpret_cast<Cand*>(diag + d.n);
         Cand* cache2 = cache + d.n;
-        int* resc = reinterpret_cast<int*>(cache2 + d.n);
-        jacobi_problem<false>(a, 0, 1, sh, diag, cache, cache2, resc);
+        int* cachef = reinterpret_cast<int*>(cache2 + d.n);
+        int* resc = cachef + d.n;
+        jacobi_problem<false, MR>(a, 0, 1, sh, diag, cache, cache2, cachef, resc);
         __syncthreads();
     }
 }
@@ -988,20 +1146,39 @@ cudaError_t launch_jacobi(const JacArgs& a, int P, cudaStream_t st) {
     return cudaLaunchKernelEx(&cfg, jacobi_single_kernel<true>, a);
 }
 
+template <int MR>
+static cudaError_t launch_batched_mr(const BatchDesc* d_desc, int nb, const int* d_order, int* d_counter,
+                                     int pivot, int stop, double tol, long long max_rot_per_n2,
+                                     long long budget_cycles, size_t smem, int ctas, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_batched_kernel<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    // no more CTAs than can be resident at once (the queue feeds them all)
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_batched_kernel<MR>, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (ctas > sms * per_sm) ctas = sms * per_sm;
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    jacobi_batched_kernel<MR><<<ctas, NT, smem, st>>>(d_desc, nb, d_order, d_counter, pivot, stop, tol,
+                                                      max_rot_per_n2, budget_cycles);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_jacobi_batched(const BatchDesc* d_desc, int nb, const int* d_order,
                                   int* d_counter, int pivot, int stop, double tol,
                                   long long max_rot_per_n2, long long budget_cycles, int max_n,
                                   int ctas, cudaStream_t st) {
     if (max_n > NT * MAXR) return cudaErrorInvalidValue;
     size_t smem = jacobi_smem_bytes(max_n, 1);
-    cudaError_t e = cudaFuncSetAttribute(jacobi_batched_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    jacobi_batched_kernel<<<ctas, NT, smem, st>>>(d_desc, nb, d_order, d_counter, pivot, stop,
-                                                  tol, max_rot_per_n2, budget_cycles);
-    return cudaGetLastError();
+    if (max_n <= NT)
+        return launch_batched_mr<1>(d_desc, nb, d_order, d_counter, pivot, stop, tol, max_rot_per_n2,
+                                    budget_cycles, smem, ctas, st);
+    return launch_batched_mr<MAXR>(d_desc, nb, d_order, d_counter, pivot, stop, tol, max_rot_per_n2,
+                                   budget_cycles, smem, ctas, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1116,9 +1293,9 @@ __global__ void info_single_kernel(const DevInfo* src, pjac_info* dst) {
 
 #ifdef PJAC_PROFILE
 extern "C" int pjac_prof_read(unsigned long long* out, int reset) {
-    cudaMemcpyFromSymbol(out, g_prof, sizeof(unsigned long long) * 24);
+    cudaMemcpyFromSymbol(out, g_prof, sizeof(unsigned long long) * 40);
     if (reset) {
-        unsigned long long z[24] = {0};
+        unsigned long long z[40] = {0};
         cudaMemcpyToSymbol(g_prof, z, sizeof(z));
     }
     return 0;
