@@ -621,13 +621,130 @@ def run_batched_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# serving form: Poisson arrivals of mixed sizes, continuous batching
+# ----------------------------------------------------------------------------
+SERVING_METRIC = "served eigensolves/s with p50/p99 latency (Poisson 2000 req/s, n in {64..2048})"
+
+
+def serving_config(count):
+    return {"workload": "serving: the first %d requests of the seeded Poisson stream (2000 req/s, seed 2), "
+                        "n in {64,128,256,512,1024,2048} with p = {.3,.25,.2,.12,.08,.05}, clustered spectra "
+                        "(n/8 clusters, spread 1e-8), 4 distinct matrices per size; gap rule, off-diagonal "
+                        "stop 1e-15, eigenvalues and vectors, host buffers in and out" % count,
+            "requests": count, "rate_per_s": 2000.0,
+            "l2": "each request's matrix is uploaded from host memory when admitted",
+            "parallelism": "single GPU: micro-batched n <= 256, one cluster per larger request"}
+
+
+def run_serving(args, ws, rank, local):
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    count = args.requests
+    t_arr, sidx, pool = pin.serving_workload(count=count)
+    sizes = pin.SERVE_SIZES
+    srv = pjac.Server(max_slots=64)
+
+    def serve(reqs, arrivals, record=True):
+        """Submit reqs at their arrival offsets, poll until all finish."""
+        out = [None] * len(reqs)
+        lat = [0.0] * len(reqs)
+        pending = {}
+        t0 = time.perf_counter()
+        nxt = 0
+        done = 0
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                tk = srv.submit(reqs[nxt], "gap", 1e-15)
+                if tk < 0:
+                    break                      # queue full: retry on the next pass
+                pending[tk] = (nxt, t0 + arrivals[nxt])
+                nxt += 1
+            srv.progress()
+            for tk in list(pending):
+                st, info, w, v = srv.poll(tk)
+                if st == pjac.PJAC_PENDING:
+                    continue
+                r, ta = pending.pop(tk)
+                lat[r] = time.perf_counter() - ta
+                out[r] = (st, w)
+                done += 1
+            time.sleep(0.0002)
+        return out, lat, time.perf_counter() - t0
+
+    # warm-up: a few small requests through the same server
+    warm = [pool[k][0].a for k in range(3)] * max(1, args.warmup)
+    serve(warm, [0.0] * len(warm), record=False)
+    reqs = [pool[s][r % len(pool[s])].a for r, s in enumerate(sidx)]
+    clk = Clocks(local)
+    clk.start()
+    out, lat, span = serve(reqs, t_arr)
+    clocks = clk.stop()
+    stats = srv.stats()
+    srv.close()
+    worst = 0.0
+    ok = True
+    for r, (st, w) in enumerate(out):
+        p = pool[sidx[r]][r % len(pool[sidx[r]])]
+        ok = ok and st == 0
+        worst = max(worst, float(np.max(np.abs(w - p.lam))) / p.norm2)
+    lat_ms = np.array(lat) * 1000.0
+
+    # the plain one-at-a-time FP64 GPU path: one solve per size timed, then a
+    # first-come-first-served queue of the same arrivals
+    h = pjac.Handle(transform="fp64")
+    per_size = {}
+    for k, m in enumerate(sizes):
+        if not np.any(sidx == k):
+            continue
+        a = torch.tensor(pool[k][0].a, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pjac.pjac_solve(h, a, "gap", 1e-15)
+        torch.cuda.synchronize()
+        per_size[m] = time.perf_counter() - t0
+    h.close()
+    fin = 0.0
+    lat1 = []
+    for r in range(count):
+        start = max(t_arr[r], fin)
+        fin = start + per_size[sizes[sidx[r]]]
+        lat1.append(fin - t_arr[r])
+    lat1 = np.array(lat1) * 1000.0
+    value = count / span
+    nbytes = int(sum(8 * sizes[s] ** 2 for s in sidx))
+    out_line = {"metric": SERVING_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": 1,
+                "warmup": args.warmup, "ms_per_step": span * 1000.0, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": serving_config(count),
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                               "max": float(lat_ms.max()),
+                               "library_p50": stats["p50_ms"], "library_p99": stats["p99_ms"]},
+                "per_size_count": {str(m): int(np.sum(sidx == k)) for k, m in enumerate(sizes)},
+                "accuracy": {"max_rel_eig_err": worst, "ok_1e-13": worst <= 1e-13, "all_status_ok": ok},
+                "one_at_a_time_fp64": {"solves_per_s": count / (fin - t_arr[0]),
+                                       "p50_ms": float(np.percentile(lat1, 50)),
+                                       "p99_ms": float(np.percentile(lat1, 99)),
+                                       "solve_s_per_size": per_size,
+                                       "how": "one pjac_solve per size timed with the FP64 transform; latencies of a "
+                                              "first-come-first-served queue of the same arrivals"},
+                "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": nbytes},
+                "gpu_launches": None, "clocks": clocks,
+                "peak_inflight": stats["peak_inflight"]}
+    if rank == 0:
+        print(json.dumps(out_line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "batched", "product"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "batched", "product", "serving"])
     ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
     ap.add_argument("--with-4096", action="store_true", help="add one timed n=4096 (cfg3) solve")
@@ -635,10 +752,13 @@ def main():
     ap.add_argument("--ref-rotations", type=int, default=100000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=300, help="serving: requests of the stream to replay")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.workload == "product":
         run_product(args, ws, rank, local)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     elif args.workload == "batched":
         if args.impl == "reference":
             run_batched_reference(args, ws, rank)

@@ -32,16 +32,18 @@ int cuda_err(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return pjac::cuda_err(e_, #call);    \
     } while (0)
 
-// Grow-only device buffer.
+// Grow-only device buffer.  Growth is stream-ordered (cudaFreeAsync /
+// cudaMallocAsync on the caller's stream), so it never waits for work of
+// other streams.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
-    int ensure(size_t need) {
+    int ensure(size_t need, cudaStream_t st) {
         if (need <= bytes) return PJAC_OK;
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, st);
         p = nullptr;
         bytes = 0;
-        cudaError_t e = cudaMalloc(&p, need);
+        cudaError_t e = cudaMallocAsync(&p, need, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_err(PJAC_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
@@ -61,6 +63,7 @@ struct pjac_handle {
     int device;
     DevBuf ws;          // main workspace
     DevBuf tcws;        // tensor-core product workspace
+    int coop_cap = 0;   // cap of the cooperative grids (0: the whole GPU)
     cudaEvent_t ev[4];
     std::mutex mu;
 };
@@ -118,6 +121,7 @@ extern "C" int pjac_create(pjac_handle** h, const pjac_opts* o) {
 void pjac_batched_release(const void* h);
 
 namespace pjac {
+void handle_set_coop_cap(pjac_handle* h, int max_grid) { h->coop_cap = max_grid; }
 int handle_opts(const pjac_handle* h, pjac_opts* o) {
     *o = h->opts;
     return PJAC_OK;
@@ -176,13 +180,13 @@ struct SolveWs {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static int layout_ws(pjac_handle* h, int n, SolveWs* w) {
+static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     size_t nn = (size_t)n * n;
     size_t sz[10] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
                      diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo)};
     size_t tot = 0;
     for (size_t s : sz) tot += align256(s);
-    int r = h->ws.ensure(tot);
+    int r = h->ws.ensure(tot, st);
     if (r) return r;
     char* p = static_cast<char*>(h->ws.p);
     void* ptrs[10];
@@ -210,7 +214,7 @@ static int tc_prepare(pjac_handle* h, int m, int n, int k, cudaStream_t st) {
     size_t need = gemm_split_bf16_ws(m, n, k);
     if (need == 0)
         return set_err(PJAC_ENOTIMPL, "split-BF16 product not available for inner dimension %d", k);
-    int r = h->tcws.ensure(need);
+    int r = h->tcws.ensure(need, st);
     if (r) return r;
     CK(cudaMemsetAsync(gemm_split_bf16_errflag(h->tcws.p), 0, sizeof(int), st));
     return PJAC_OK;
@@ -283,7 +287,7 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         // (Newton--Schulz), then a refinement pass on B = X^T fl32(A) X
         // that diagonalises it further, X <- X (I + D).  After the final
         // reorthogonalisation below, fl32(A) = Q Lambda Q^T to FP32 accuracy.
-        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, st));
+        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, h->coop_cap, st));
         CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
         int r = newton_schulz(h, Q, ldq, n, 2, w, st);
         if (r) return r;
@@ -293,7 +297,7 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
         if (r) return r;
         CK(symmetrize(w.Y, n, n, st));
-        CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, st));                        // D
+        CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, h->coop_cap, st));                        // D
         CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
         r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);    // X D
         if (r) return r;
@@ -322,7 +326,7 @@ extern "C" int pjac_precondition(pjac_handle* h, const double* A, int n, int lda
     std::lock_guard<std::mutex> lk(h->mu);
     cudaStream_t st = (cudaStream_t)stream;
     SolveWs w;
-    r = layout_ws(h, n, &w);
+    r = layout_ws(h, n, &w, st);
     if (r) return r;
     r = check_input(h, A, lda, n, st, w.flag);
     if (r) return r;
@@ -452,7 +456,7 @@ extern "C" int pjac_solve(pjac_handle* h, const double* A, int n, int lda, pjac_
     if (n == 1) return trivial_n1(A, W, V, st, info);
     std::lock_guard<std::mutex> lk(h->mu);
     SolveWs w;
-    r = layout_ws(h, n, &w);
+    r = layout_ws(h, n, &w, st);
     if (r) return r;
     r = check_input(h, A, lda, n, st, w.flag);
     if (r) return r;
@@ -471,7 +475,7 @@ int solve_async_dev(pjac_handle* h, const double* A, int n, int lda, pjac_pivot 
     if (r) return r;
     std::lock_guard<std::mutex> lk(h->mu);
     SolveWs w;
-    r = layout_ws(h, n, &w);
+    r = layout_ws(h, n, &w, st);
     if (r) return r;
     r = solve_pipeline(h, A, n, lda, pivot, tol, W, V, ldv, w, st);
     if (r) return r;
@@ -496,7 +500,7 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
     if (n == 1) return trivial_n1(A1, W, V, st, info);
     std::lock_guard<std::mutex> lk(h->mu);
     SolveWs w;
-    r = layout_ws(h, n, &w);
+    r = layout_ws(h, n, &w, st);
     if (r) return r;
     r = check_input(h, A1, lda1, n, st, w.flag);
     if (r) return r;

@@ -324,10 +324,11 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     std::lock_guard<std::mutex> lk(g_bmu);
     BatchState& bs = g_bstate[h];
     if (bs.dbytes < need) {
-        if (bs.dbuf) cudaFree(bs.dbuf);
+        // stream-ordered: growing never waits for other streams' work
+        if (bs.dbuf) cudaFreeAsync(bs.dbuf, st);
         bs.dbuf = nullptr;
         bs.dbytes = 0;
-        cudaError_t e = cudaMalloc(&bs.dbuf, need);
+        cudaError_t e = cudaMallocAsync(&bs.dbuf, need, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_err(PJAC_ENOMEM, "batched workspace of %zu bytes: %s", need, cudaGetErrorString(e));
@@ -345,7 +346,8 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     if (ec != cudaSuccess) return cuda_err(ec, "cudaStreamIsCapturing");
     const bool capturing = cap != cudaStreamCaptureStatusNone;
     if (bs.hbytes < hneed) {
-        if (bs.hbuf) cudaFreeHost(bs.hbuf);
+        // retired, not freed: cudaFreeHost would wait for the whole device
+        if (bs.hbuf) bs.held.push_back(bs.hbuf);
         bs.hbuf = nullptr;
         bs.hbytes = 0;
         cudaError_t e = cudaMallocHost(&bs.hbuf, hneed);

@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(256) refine32_coop_kernel(const double* __rest
     }
 }
 
-cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, cudaStream_t st) {
+cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, int max_grid,
+                        cudaStream_t st) {
     int npad = ((n + 31) / 32) * 32;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -393,6 +394,7 @@ cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_
     if (e != cudaSuccess) return e;
     int T = npad / 32;
     int grid = std::min(sms * std::max(1, std::min(per_sm, 4)), 2 * T * T);
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;   // share the GPU (all CTAs must be co-resident)
     void* args[] = {(void*)&B, (void*)&n, (void*)&npad, (void*)&ws, (void*)&Dout, (void*)&max_sweeps};
     return cudaLaunchCooperativeKernel((const void*)refine32_coop_kernel, dim3(grid), dim3(256), args, 0, st);
 }
@@ -406,7 +408,7 @@ size_t diag_fp32_ws_floats(int n) {
 // Q0 <- eigenvectors of fl32(A) (approximately).  ws: diag_fp32_ws_floats(n)
 // floats.  One cooperative launch; nothing waits on the host.
 cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
-                      int max_sweeps, cudaStream_t st) {
+                      int max_sweeps, int max_grid, cudaStream_t st) {
     (void)iws;
     int npad = ((n + 31) / 32) * 32;
     long long nn = (long long)npad * npad;
@@ -424,6 +426,7 @@ cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* w
     if (e != cudaSuccess) return e;
     int T = npad / 32;
     int grid = std::min(sms * std::max(1, std::min(per_sm, 4)), 2 * T * T);
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;   // share the GPU (all CTAs must be co-resident)
     void* args[] = {(void*)&A, (void*)&lda, (void*)&n, (void*)&npad, (void*)&Ab0, (void*)&Ab1, (void*)&Qb0,
                     (void*)&Qb1, (void*)&Q0, (void*)&acc, (void*)&max_sweeps};
     return cudaLaunchCooperativeKernel((const void*)diag32_coop_kernel, dim3(grid), dim3(256), args, 0, st);

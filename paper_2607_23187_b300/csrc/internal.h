@@ -90,11 +90,15 @@ int gemm_split_bf16_launches(int m, int n, int k);      // kernel launches per p
 cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st);
 
 // diag32.cu: FP32 parallel-order Jacobi diagonalisation of fl32(A); Q0 out (ld n)
+// max_grid > 0 caps the cooperative grid (so that it can start beside other work)
 cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
-                      int max_sweeps, cudaStream_t st);
+                      int max_sweeps, int max_grid, cudaStream_t st);
 size_t diag_fp32_ws_floats(int n);
 // refinement of an FP32 eigenbasis on B = X^T fl32(A) X; Dout: X (I + D)
-cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, cudaStream_t st);
+cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, int max_grid,
+                        cudaStream_t st);
+// serving lanes: cap of the cooperative grids of a handle's preconditioner
+void handle_set_coop_cap(pjac_handle* h, int max_grid);
 cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st);
 cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st);
 

@@ -297,9 +297,13 @@ __device__ Cand block_select(Cand mine, int pivot, const double* diag, Sh& sh) {
 
 // Phase 2 of a block selection: exact argmax among the contenders (uniform
 // call, used when several threads are within the tie band).
-__device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag, Sh& sh) {
+__device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag, Sh& sh, Cand* wb = nullptr) {
     double v = -2.0;
-    if (cont) v = cand_value(mine, pivot, diag);
+    if (cont) {
+        v = cand_value(mine, pivot, diag);
+        // keep the exact score with the cached entry it came from
+        if (wb && wb->row == mine.row && wb->col == mine.col) wb->ex = mine.ex;
+    }
     int lane = threadIdx.x & 31;
     double bv = v;
     int br = mine.row, bc = mine.col, bl = lane;
@@ -340,7 +344,7 @@ __device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag
 // the contender counts, one for the results; the exact phase runs only for
 // a kind with several contenders.  Uniform call.
 __device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh,
-                              int (&kA)[2], int (&kB)[2]) {
+                              int (&kA)[2], int (&kB)[2], Cand* wb0 = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tie = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_GAP_TIE;
     int w0 = __reduce_max_sync(0xffffffffu, c0.key);
@@ -416,7 +420,7 @@ __device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const dou
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         r[q] = (cnt[q] == 1 || one_pair[q]) ? sh.out3[q] : no_cand();
-        if (cnt[q] > 1 && !one_pair[q]) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh);
+        if (cnt[q] > 1 && !one_pair[q]) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh, q == 0 ? wb0 : nullptr);
     }
     c0 = r[0];
     c1 = r[1];
@@ -1004,11 +1008,12 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 int k = k0 + tid + r * NT;
                 if (k >= k1) break;
                 if (k == i || k == j) continue;
-                Cand cc = cache[k - k0];
+                Cand& cc = cache[k - k0];   // exact scores computed here stay in the cache
                 if (better(cc, loc, pivot, diag)) loc = cc;
             }
+            Cand* wb = (loc.key != KEY_NONE) ? &cache[loc.row - k0] : nullptr;
             SLAP(2);
-            block_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ);
+            block_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ, wb);
             LAP(4);
             publish_select(loc, pI, pJ, kI, kJ, i, j);
             LAP(6);

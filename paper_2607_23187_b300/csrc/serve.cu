@@ -74,26 +74,39 @@ struct Lane {
     pjac_info* hInfo = nullptr; size_t hInfo_bytes = 0;
     std::vector<int> ns;
     std::vector<int64_t> aoff, woff;
+    std::vector<void*> retired;   // outgrown pinned buffers, freed when the server is destroyed
     size_t footprint = 0;
     int launch_status = PJAC_OK;
 };
 
+// Lane buffers grow to the next power of two, stream-ordered on the lane's
+// stream (device) so that growing never waits for other lanes' work.
+size_t pow2_at_least(size_t x) {
+    size_t p = 4096;
+    while (p < x) p <<= 1;
+    return p;
+}
+
 template <class T>
-int grow_dev(T*& p, size_t& cur, size_t need) {
+int grow_dev(T*& p, size_t& cur, size_t need, cudaStream_t st) {
     if (need <= cur) return PJAC_OK;
-    if (p) cudaFree(p);
+    need = pow2_at_least(need);
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     cur = 0;
-    cudaError_t e = cudaMalloc((void**)&p, need);
+    cudaError_t e = cudaMallocAsync((void**)&p, need, st);
     if (e != cudaSuccess) { cudaGetLastError(); return set_err(PJAC_ENOMEM, "serve: cudaMalloc %zu", need); }
     cur = need;
     return PJAC_OK;
 }
 
+// Pinned host buffers are never freed while the server runs (cudaFreeHost
+// waits for the whole device): an outgrown one is retired.
 template <class T>
-int grow_host(T*& p, size_t& cur, size_t need) {
+int grow_host(T*& p, size_t& cur, size_t need, std::vector<void*>& retired) {
     if (need <= cur) return PJAC_OK;
-    if (p) cudaFreeHost(p);
+    need = pow2_at_least(need);
+    if (p) retired.push_back(p);
     p = nullptr;
     cur = 0;
     cudaError_t e = cudaMallocHost((void**)&p, need);
@@ -151,6 +164,9 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
     sv->lanes.resize(d.max_slots);
     for (auto& L : sv->lanes) {
         int r = pjac_create(&L.h, &d.solver);
+        // a served request's preconditioner must start beside running solves:
+        // its cooperative kernels use at most 64 CTAs instead of the whole GPU
+        if (r == PJAC_OK) handle_set_coop_cap(L.h, 64);
         cudaError_t e1 = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
         cudaError_t e2 = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
         if (r != PJAC_OK || e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -173,6 +189,7 @@ extern "C" int pjac_serve_destroy(pjac_server* s) {
         if (L.done) cudaEventDestroy(L.done);
         cudaFree(L.dA); cudaFree(L.dW); cudaFree(L.dV); cudaFree(L.dInfo);
         cudaFreeHost(L.hA); cudaFreeHost(L.hW); cudaFreeHost(L.hV); cudaFreeHost(L.hInfo);
+        for (void* q : L.retired) cudaFreeHost(q);
     }
     for (auto& kv : s->all) delete kv.second;
     delete s;
@@ -193,14 +210,14 @@ static int launch_lane(pjac_server* s, Lane& L) {
         totW += (size_t)n;
     }
     int r = PJAC_OK;
-    if ((r = grow_dev(L.dA, L.dA_bytes, totA * 8))) return r;
-    if ((r = grow_dev(L.dV, L.dV_bytes, totA * 8))) return r;
-    if ((r = grow_dev(L.dW, L.dW_bytes, totW * 8))) return r;
-    if ((r = grow_dev(L.dInfo, L.dInfo_bytes, sizeof(pjac_info) * nb))) return r;
-    if ((r = grow_host(L.hA, L.hA_bytes, totA * 8))) return r;
-    if ((r = grow_host(L.hV, L.hV_bytes, totA * 8))) return r;
-    if ((r = grow_host(L.hW, L.hW_bytes, totW * 8))) return r;
-    if ((r = grow_host(L.hInfo, L.hInfo_bytes, sizeof(pjac_info) * nb))) return r;
+    if ((r = grow_dev(L.dA, L.dA_bytes, totA * 8, L.st))) return r;
+    if ((r = grow_dev(L.dV, L.dV_bytes, totA * 8, L.st))) return r;
+    if ((r = grow_dev(L.dW, L.dW_bytes, totW * 8, L.st))) return r;
+    if ((r = grow_dev(L.dInfo, L.dInfo_bytes, sizeof(pjac_info) * nb, L.st))) return r;
+    if ((r = grow_host(L.hA, L.hA_bytes, totA * 8, L.retired))) return r;
+    if ((r = grow_host(L.hV, L.hV_bytes, totA * 8, L.retired))) return r;
+    if ((r = grow_host(L.hW, L.hW_bytes, totW * 8, L.retired))) return r;
+    if ((r = grow_host(L.hInfo, L.hInfo_bytes, sizeof(pjac_info) * nb, L.retired))) return r;
     for (int k = 0; k < nb; ++k)
         memcpy(L.hA + L.aoff[k], L.reqs[k]->a.data(), (size_t)L.ns[k] * L.ns[k] * 8);
     cudaError_t e = cudaMemcpyAsync(L.dA, L.hA, totA * 8, cudaMemcpyHostToDevice, L.st);
