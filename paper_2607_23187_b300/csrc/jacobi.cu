@@ -77,6 +77,7 @@ struct Sh {
     Cand sel;
     int tflag, pad3;
     double c, s, t, dii, djj, q;
+    double old_di, old_dj;  // diagonal entries before the pending rotation
     double normf, thr, eps_li, scale;
     int pi, pj, nresc, decision;
     int key_eps, pad2;
@@ -537,16 +538,27 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, 
 
 // off(A)^2 * 2^-2e over the owned rows, e = ilogb(||A1||_F) (as the oracle).
 __device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, Sh& sh) {
-    double acc = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        const double* row = a.A + (long long)k * a.lda;
+    // eight independent partial sums over eight rows at a time: the loads of
+    // a block overlap and no FMA waits on the previous one
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = k0; k < k1; k += 8) {
         for (int l = threadIdx.x; l < a.n; l += NT) {
-            if (l == k) continue;
-            double x = __dmul_rn(ldcg(row + l), scale);
-            acc = __fma_rn(x, x, acc);
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int kk = k + u;
+                x[u] = (kk < k1 && kk != l) ? ldcg(a.A + (long long)kk * a.lda + l) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const double y = __dmul_rn(x[u], scale);
+                acc[u] = __fma_rn(y, y, acc[u]);
+            }
         }
     }
-    return block_sum(acc, sh);
+    double t = __dadd_rn(__dadd_rn(__dadd_rn(acc[0], acc[1]), __dadd_rn(acc[2], acc[3])),
+                         __dadd_rn(__dadd_rn(acc[4], acc[5]), __dadd_rn(acc[6], acc[7])));
+    return block_sum(t, sh);
 }
 
 // Solve one problem.  rank/P: this CTA's rank in the cluster and the
@@ -819,6 +831,11 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; cachef[k - k0] = F; }
         }
         __syncthreads();
+        // The pending pivot, the same in every thread after publish_select:
+        // pdec (0 rotate, 1 converged, 2 time budget, 3 rotation budget),
+        // indices and rotation.
+        int pdec = 1, ppi = 0, ppj = 0;
+        double pend_c = 1.0, pend_s = 0.0;
         // Publish this CTA's three candidates (best own row, its part of row
         // i, its part of row j) with their exact scores and rotations --
         // evaluated by three lanes at once, from one shared denominator --
@@ -830,21 +847,21 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                                   int j) {
             if (tid < 3) {
                 Cand c = (tid == 0) ? loc : (tid == 1 ? pI : pJ);
-                double pc = 1.0, ps = 0.0, pt = 0.0;
+                double rc = 1.0, rs = 0.0, rt = 0.0;
                 if (c.key != KEY_NONE) {
                     int ci = min(c.row, c.col), cj = max(c.row, c.col);
                     Eval ev = eval_pair(diag[ci], diag[cj], c.x);
                     if (pivot != PJAC_PIVOT_GREEDY) c.ex = ev.l;
-                    pc = ev.c;
-                    ps = ev.s;
-                    pt = ev.t;
+                    rc = ev.c;
+                    rs = ev.s;
+                    rt = ev.t;
                 }
                 if (tid == 0) sh.stage.loc = c;
                 else if (tid == 1) sh.stage.pi = c;
                 else sh.stage.pj = c;
-                sh.stage.prm[tid][0] = pc;
-                sh.stage.prm[tid][1] = ps;
-                sh.stage.prm[tid][2] = pt;
+                sh.stage.prm[tid][0] = rc;
+                sh.stage.prm[tid][1] = rs;
+                sh.stage.prm[tid][2] = rt;
                 if (tid == 0) {
                     sh.stage.sum = 0.0; sh.stage.flags = sh.tflag; sh.stage.pad = 0;
                     sh.stage.ki[0] = kI[0]; sh.stage.ki[1] = kI[1];
@@ -867,54 +884,82 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             const int warp = tid >> 5, lane = tid & 31;
             int width = 1;
             while (width < P) width <<= 1;
-            if (warp < 3) {
+            if (warp == 0) {
+                // the winner over all 3P published candidates, and the
+                // decision on it, broadcast through shared memory
+                Cand g = no_cand();
+                for (int e = lane; e < 3 * P; e += 32) {
+                    const Slot& sl = sh.inbox[par][e / 3];
+                    const int q3 = e - 3 * (e / 3);
+                    Cand c = (q3 == 0) ? sl.loc : (q3 == 1 ? sl.pi : sl.pj);
+                    c.pad = e;
+                    if (better(c, g, pivot, diag)) g = c;
+                }
+                int w3 = 1;
+                while (w3 < 3 * P && w3 < 32) w3 <<= 1;
+                g = warp_best(g, w3, pivot, diag);
+                if (lane == 0) {
+                    double v = -1.0;
+                    int dec = 0;
+                    if (g.key == KEY_NONE) dec = 1;   // n < 2
+                    else if (pivot == PJAC_PIVOT_GREEDY) {
+                        v = fabs(g.x);
+                        if (v == 0.0) dec = 1;
+                    } else {
+                        v = cand_value(g, pivot, diag);   // exact score published with the candidate
+                        if (v == 0.0) dec = 1;
+                        if (!dec && a.stop == PJAC_STOP_LIBOUND && v <= sh.eps_li) dec = 1;
+                    }
+                    if (!dec && rot >= a.max_rot) dec = 3;
+                    if (sh.inbox[par][0].flags & 1) dec = 2;   // time budget spent
+                    sh.decision = dec;
+                    sh.sel = g;
+                    if (v >= 0.0) sh.q = v;
+                    if (!dec) {
+                        const int i2 = min(g.row, g.col), j2 = max(g.row, g.col);
+                        const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
+                        sh.pi = i2;
+                        sh.pj = j2;
+                        sh.c = pr[0];
+                        sh.s = pr[1];
+                        sh.t = pr[2];
+                        // the pending rotation's diagonal, undone if the
+                        // convergence test stops before the rotation
+                        sh.old_di = diag[i2];
+                        sh.old_dj = diag[j2];
+                        diag[i2] = __fma_rn(pr[2], g.x, sh.old_di);
+                        diag[j2] = __fma_rn(-pr[2], g.x, sh.old_dj);
+                    }
+                    sh.nresc = 0;
+                }
+            } else if (i >= 0 && (warp == 1 || warp == 2)) {
+                // new heads of rows i and j and their bounds F; the owning
+                // CTA writes them into its cache
                 Cand c = no_cand();
+                int ka = KEY_NONE, kb = KEY_NONE;   // two largest keys of the row
                 if (lane < P) {
                     const Slot& sl = sh.inbox[par][lane];
-                    c = (warp == 0) ? sl.loc : (warp == 1 ? sl.pi : sl.pj);
+                    c = (warp == 1) ? sl.pi : sl.pj;
                     c.pad = lane * 3 + warp;
+                    ka = (warp == 1) ? sl.ki[0] : sl.kj[0];
+                    kb = (warp == 1) ? sl.ki[1] : sl.kj[1];
                 }
                 c = warp_best(c, width, pivot, diag);
-                if (lane == 0) sh.out3[warp] = c;
-                if (warp > 0) {
-                    // F of the new row i (row j): largest key of its entries
-                    // other than the head, from every rank's two largest keys
-                    int k1 = KEY_NONE, k2 = KEY_NONE;
-                    if (lane < P) {
-                        const Slot& sl = sh.inbox[par][lane];
-                        k1 = (warp == 1) ? sl.ki[0] : sl.kj[0];
-                        k2 = (warp == 1) ? sl.ki[1] : sl.kj[1];
-                    }
-                    warp_top2_keys(k1, k2);
-                    if (lane == 0) sh.fij[warp - 1] = bound_without_head(c, k1, k2);
+                warp_top2_keys(ka, kb);
+                const int row = (warp == 1) ? i : j;
+                if (lane == 0 && row >= k0 && row < k1) {
+                    cache[row - k0] = c;
+                    cache2[row - k0] = no_cand();
+                    cachef[row - k0] = bound_without_head(c, ka, kb);
                 }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                Cand g = sh.out3[0], bi = sh.out3[1], bj = sh.out3[2];
-                if (better(bi, g, pivot, diag)) g = bi;
-                if (better(bj, g, pivot, diag)) g = bj;
-                if (i >= k0 && i < k1) {
-                    cache[i - k0] = bi;
-                    cache2[i - k0] = no_cand();
-                    cachef[i - k0] = sh.fij[0];
-                }
-                if (j >= k0 && j < k1) {
-                    cache[j - k0] = bj;
-                    cache2[j - k0] = no_cand();
-                    cachef[j - k0] = sh.fij[1];
-                }
-                if (g.key != KEY_NONE) {
-                    const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
-                    sh.c = pr[0];
-                    sh.s = pr[1];
-                    sh.t = pr[2];
-                }
-                sh.sel = g;
-                sh.decision = (sh.inbox[par][0].flags & 1) ? 2 : 0;
             }
             par ^= 1;
             __syncthreads();
+            pdec = sh.decision;
+            ppi = sh.pi;
+            ppj = sh.pj;
+            pend_c = sh.c;
+            pend_s = sh.s;
         };
 
         // first selection
@@ -935,52 +980,25 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         bool stop_now = false;
         for (;;) {
             LAP(7);
+            if (pdec == 2) { status = PJAC_ETIMEOUT; break; }
+            if (pdec == 0) preload(ppi, ppj);   // the loads do not depend on the test below
             if (rot % ce == 0) {
                 offdiag_check(stop_now);
-                if (stop_now) break;
+                if (stop_now) {
+                    if (tid == 0 && pdec == 0) {   // the pending rotation is not applied
+                        diag[ppi] = sh.old_di;
+                        diag[ppj] = sh.old_dj;
+                    }
+                    break;
+                }
             }
             LAP(0);
-            {
-                Cand g0 = sh.sel;
-                if (g0.key != KEY_NONE) preload(min(g0.row, g0.col), max(g0.row, g0.col));
-            }
             SLAP(3);
-            // decisions on the current selection (thread 0, then broadcast);
-            // its exact score and rotation arrived with it
-            if (tid == 0) {
-                Cand g = sh.sel;
-                int dec = 0;
-                double v = -1.0;
-                if (g.key == KEY_NONE) dec = 1;   // n < 2
-                else if (pivot == PJAC_PIVOT_GREEDY) {
-                    v = fabs(g.x);
-                    if (v == 0.0) dec = 1;
-                } else {
-                    v = cand_value(g, pivot, diag);
-                    if (v == 0.0) dec = 1;
-                    if (!dec && a.stop == PJAC_STOP_LIBOUND && v <= sh.eps_li) dec = 1;
-                }
-                if (!dec && rot >= a.max_rot) dec = 3;
-                if (v >= 0.0) sh.q = v;
-                sh.decision = dec;
-                if (!dec) {
-                    int i = min(g.row, g.col), j = max(g.row, g.col);
-                    double q = g.x;
-                    sh.pi = i;
-                    sh.pj = j;
-                    sh.dii = __fma_rn(sh.t, q, diag[i]);
-                    sh.djj = __fma_rn(-sh.t, q, diag[j]);
-                    diag[i] = sh.dii;
-                    diag[j] = sh.djj;
-                }
-                sh.nresc = 0;
-            }
-            __syncthreads();
+            if (pdec == 1) { status = PJAC_OK; break; }
+            if (pdec == 3) { status = PJAC_ENOCONV; break; }
             LAP(1);
-            if (sh.decision == 1) { status = PJAC_OK; break; }
-            if (sh.decision == 3) { status = PJAC_ENOCONV; break; }
-            const int i = sh.pi, j = sh.pj;
-            const double c = sh.c, s = sh.s, dii = sh.dii, djj = sh.djj;
+            const int i = ppi, j = ppj;
+            const double c = pend_c, s = pend_s, dii = diag[i], djj = diag[j];
             Cand pI = no_cand(), pJ = no_cand();
             int kI[2] = {KEY_NONE, KEY_NONE}, kJ[2] = {KEY_NONE, KEY_NONE};
             rotate_owned(i, j, c, s, dii, djj, true, pI, pJ, kI, kJ);
@@ -1017,7 +1035,6 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             LAP(4);
             publish_select(loc, pI, pJ, kI, kJ, i, j);
             LAP(6);
-            if (sh.decision == 2) { status = PJAC_ETIMEOUT; break; }
         }
 #undef LAP
 #undef SLAP
