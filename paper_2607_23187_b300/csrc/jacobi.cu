@@ -61,12 +61,9 @@ struct Slot {
 };
 
 struct Sh {
-    int wk3[NT / 32][3];
-    int wn3[NT / 32][3];
-    int wp3[NT / 32][3][2]; // per warp: smallest and largest pair id among contenders
-    Cand out3[3];
     int fij[2];             // key bounds F of the new rows i and j
     int wkk[NT / 32][4];    // per-warp two largest keys of rows i and j
+    Cand ww[NT / 32][3];    // per-warp winners of the three selections
     int wkey[NT / 32];
     Cand wc[NT / 32];
     double wsum[NT / 32];
@@ -296,136 +293,104 @@ __device__ Cand block_select(Cand mine, int pivot, const double* diag, Sh& sh) {
     return r;
 }
 
-// Phase 2 of a block selection: exact argmax among the contenders (uniform
-// call, used when several threads are within the tie band).
-__device__ Cand block_phase2(Cand mine, bool cont, int pivot, const double* diag, Sh& sh, Cand* wb = nullptr) {
-    double v = -2.0;
-    if (cont) {
-        v = cand_value(mine, pivot, diag);
-        // keep the exact score with the cached entry it came from
-        if (wb && wb->row == mine.row && wb->col == mine.col) wb->ex = mine.ex;
-    }
-    int lane = threadIdx.x & 31;
-    double bv = v;
-    int br = mine.row, bc = mine.col, bl = lane;
+// Exact argmax of one candidate per lane over a warp (every lane gets the
+// winner), without block barriers.  Keys first; lanes whose key is within
+// the tie band of the maximum are contenders, and only several contenders
+// need their exact scores (computed in parallel; wb, when given, is the
+// cache entry the lane's candidate came from and keeps its exact score).
+// Contenders that are all one pair seen from its two rows have equal
+// scores and the row with row < col wins, as in better().
+__device__ Cand warp_select(Cand c, int pivot, const double* diag, Cand* wb) {
+    const int lane = threadIdx.x & 31;
+    const int m = __reduce_max_sync(0xffffffffu, c.key);
+    if (m == KEY_NONE) return no_cand();
+    const bool gap = pivot != PJAC_PIVOT_GREEDY;
+    const bool exact_all = gap && m < KEY_SUB;
+    const int tie = gap ? KEY_GAP_TIE : 0;
+    const bool cont = c.key != KEY_NONE && (exact_all || (long long)c.key >= (long long)m - tie);
+    const unsigned b = __ballot_sync(0xffffffffu, cont);
+    int src;
+    if (__popc(b) == 1) {
+        src = __ffs(b) - 1;
+    } else {
+        const int pid = cont ? ((min(c.row, c.col) << 15) | max(c.row, c.col)) : INT_MAX;
+        const int pmin = __reduce_min_sync(0xffffffffu, pid);
+        const int pmax = __reduce_max_sync(0xffffffffu, cont ? pid : -1);
+        if (pmin == pmax) {
+            src = __ffs(__ballot_sync(0xffffffffu, cont && c.row < c.col)) - 1;
+        } else {
+            double v = -2.0;
+            if (cont) {
+                v = cand_value(c, pivot, diag);
+                if (wb && wb->row == c.row && wb->col == c.col) wb->ex = c.ex;
+            }
+            double bv = v;
+            int br = cont ? c.row : INT_MAX, bc = cont ? c.col : INT_MAX, bl = lane;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, off);
-        int orr = __shfl_xor_sync(0xffffffffu, br, off);
-        int oc = __shfl_xor_sync(0xffffffffu, bc, off);
-        int ol = __shfl_xor_sync(0xffffffffu, bl, off);
-        bool take = (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
-        if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
-    }
-    if (lane == bl) {
-        Cand w = mine;
-        if (bv < -1.0) w.key = KEY_NONE;
-        sh.wc[threadIdx.x >> 5] = w;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Cand best = no_cand();
-        double vb = -2.0;
-        for (int w = 0; w < NT / 32; ++w) {
-            Cand c = sh.wc[w];
-            if (c.key == KEY_NONE) continue;
-            double vc = cand_value(c, pivot, diag);
-            if (best.key == KEY_NONE || exact_better(vc, c, vb, best)) { best = c; vb = vc; }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, off);
+                const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+                const bool take =
+                    (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
+                if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
+            }
+            src = bl;
         }
-        sh.out = best;
     }
-    __syncthreads();
-    Cand r = sh.out;
-    __syncthreads();
+    Cand r;
+    r.key = __shfl_sync(0xffffffffu, c.key, src);
+    r.row = __shfl_sync(0xffffffffu, c.row, src);
+    r.col = __shfl_sync(0xffffffffu, c.col, src);
+    r.pad = __shfl_sync(0xffffffffu, c.pad, src);
+    r.x = __shfl_sync(0xffffffffu, c.x, src);
+    r.ex = __shfl_sync(0xffffffffu, c.ex, src);
     return r;
 }
 
-// Three independent block-wide exact argmaxes (one candidate of each kind
-// per thread) in one pass: one barrier for the three maximum keys, one for
-// the contender counts, one for the results; the exact phase runs only for
-// a kind with several contenders.  Uniform call.
-__device__ void block_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh,
-                              int (&kA)[2], int (&kB)[2], Cand* wb0 = nullptr) {
+// The CTA's three exact argmaxes (best own row, its part of row i, of row j)
+// and the two largest keys of its parts of rows i and j, with one block
+// barrier: every warp selects its own winners, then warp 0 selects among
+// the warps' winners.  The results are valid in warp 0 only (the warp that
+// evaluates and publishes them).  cache/k0/k1: the row cache, so that exact
+// scores computed in warp 0 stay with the cached entries.
+__device__ void cta_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const double* diag, Sh& sh,
+                            int (&kA)[2], int (&kB)[2], Cand* wb0, Cand* cache, int k0, int k1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tie = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_GAP_TIE;
-    int w0 = __reduce_max_sync(0xffffffffu, c0.key);
-    int w1 = __reduce_max_sync(0xffffffffu, c1.key);
-    int w2 = __reduce_max_sync(0xffffffffu, c2.key);
+    const Cand w0 = warp_select(c0, pivot, diag, wb0);
+    const Cand w1 = warp_select(c1, pivot, diag, nullptr);
+    const Cand w2 = warp_select(c2, pivot, diag, nullptr);
     warp_top2_keys(kA[0], kA[1]);
     warp_top2_keys(kB[0], kB[1]);
     if (lane == 0) {
-        sh.wk3[warp][0] = w0; sh.wk3[warp][1] = w1; sh.wk3[warp][2] = w2;
+        sh.ww[warp][0] = w0;
+        sh.ww[warp][1] = w1;
+        sh.ww[warp][2] = w2;
         sh.wkk[warp][0] = kA[0]; sh.wkk[warp][1] = kA[1]; sh.wkk[warp][2] = kB[0]; sh.wkk[warp][3] = kB[1];
     }
     __syncthreads();
-    // the two largest keys of kA and kB over the block (every thread)
-    {
-        int a1 = KEY_NONE, a2 = KEY_NONE, b1 = KEY_NONE, b2 = KEY_NONE;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) {
-            key_push(sh.wkk[w][0], a1, a2);
-            key_push(sh.wkk[w][1], a1, a2);
-            key_push(sh.wkk[w][2], b1, b2);
-            key_push(sh.wkk[w][3], b1, b2);
-        }
-        kA[0] = a1; kA[1] = a2; kB[0] = b1; kB[1] = b2;
-    }
-    int m[3] = {sh.wk3[0][0], sh.wk3[0][1], sh.wk3[0][2]};
-#pragma unroll
-    for (int w = 1; w < NT / 32; ++w) {
-        m[0] = max(m[0], sh.wk3[w][0]);
-        m[1] = max(m[1], sh.wk3[w][1]);
-        m[2] = max(m[2], sh.wk3[w][2]);
-    }
-    Cand cs[3] = {c0, c1, c2};
-    bool t[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        bool exact_all = (pivot != PJAC_PIVOT_GREEDY) && m[q] < KEY_SUB;
-        t[q] = m[q] != KEY_NONE && cs[q].key != KEY_NONE &&
-               (exact_all || (long long)cs[q].key >= (long long)m[q] - tie);
-        unsigned b = __ballot_sync(0xffffffffu, t[q]);
-        // unordered pair id (indices < 2^15) of the contenders
-        const int pid = t[q] ? ((min(cs[q].row, cs[q].col) << 15) | max(cs[q].row, cs[q].col)) : INT_MAX;
-        const int pmin = __reduce_min_sync(0xffffffffu, pid);
-        const int pmax = __reduce_max_sync(0xffffffffu, t[q] ? pid : -1);
-        if (lane == 0) {
-            sh.wn3[warp][q] = __popc(b);
-            sh.wp3[warp][q][0] = pmin;
-            sh.wp3[warp][q][1] = pmax;
-        }
-    }
-    __syncthreads();
-    int cnt[3] = {0, 0, 0};
-    bool one_pair[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        int gmin = INT_MAX, gmax = -1;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) {
-            cnt[q] += sh.wn3[w][q];
-            gmin = min(gmin, sh.wp3[w][q][0]);
-            gmax = max(gmax, sh.wp3[w][q][1]);
-        }
-        // several contenders that are all the same pair seen from its two
-        // rows: equal scores, the row with row < col wins (as in better())
-        one_pair[q] = cnt[q] > 1 && gmin == gmax;
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        if (cnt[q] == 1 && t[q]) sh.out3[q] = cs[q];
-        if (one_pair[q] && t[q] && cs[q].row < cs[q].col) sh.out3[q] = cs[q];
-    }
-    __syncthreads();
+    if (warp != 0) return;
     Cand r[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        r[q] = (cnt[q] == 1 || one_pair[q]) ? sh.out3[q] : no_cand();
-        if (cnt[q] > 1 && !one_pair[q]) r[q] = block_phase2(cs[q], t[q], pivot, diag, sh, q == 0 ? wb0 : nullptr);
+        Cand c = (lane < NT / 32) ? sh.ww[lane][q] : no_cand();
+        Cand* wb = nullptr;
+        if (q == 0 && c.key != KEY_NONE && c.row >= k0 && c.row < k1) wb = &cache[c.row - k0];
+        r[q] = warp_select(c, pivot, diag, wb);
     }
     c0 = r[0];
     c1 = r[1];
     c2 = r[2];
+    int a1 = KEY_NONE, a2 = KEY_NONE, b1 = KEY_NONE, b2 = KEY_NONE;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        key_push(sh.wkk[w][0], a1, a2);
+        key_push(sh.wkk[w][1], a1, a2);
+        key_push(sh.wkk[w][2], b1, b2);
+        key_push(sh.wkk[w][3], b1, b2);
+    }
+    kA[0] = a1; kA[1] = a2; kB[0] = b1; kB[1] = b2;
 }
 
 // Best candidate over the first `width` lanes of a warp (width a power of
@@ -1031,7 +996,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             }
             Cand* wb = (loc.key != KEY_NONE) ? &cache[loc.row - k0] : nullptr;
             SLAP(2);
-            block_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ, wb);
+            cta_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ, wb, cache, k0, k1);
             LAP(4);
             publish_select(loc, pI, pJ, kI, kJ, i, j);
             LAP(6);
