@@ -642,7 +642,8 @@ def serving_config(count):
                         "stop 1e-15, eigenvalues and vectors, host buffers in and out" % count,
             "requests": count, "rate_per_s": 2000.0,
             "l2": "each request's matrix is uploaded from host memory when admitted",
-            "parallelism": "single GPU: micro-batched n <= 256, one cluster per larger request"}
+            "parallelism": "single GPU: micro-batched n <= 256, one cluster per larger request; 32 lanes "
+                           "(4 high-priority), CUDA_DEVICE_MAX_CONNECTIONS=32"}
 
 
 def run_serving(args, ws, rank, local):
@@ -653,7 +654,7 @@ def run_serving(args, ws, rank, local):
     count = args.requests
     t_arr, sidx, pool = pin.serving_workload(count=count)
     sizes = pin.SERVE_SIZES
-    srv = pjac.Server(max_slots=64)
+    srv = pjac.Server(max_slots=32)
 
     def serve(reqs, arrivals, record=True):
         """Submit reqs at their arrival offsets, poll until all finish."""
@@ -700,6 +701,7 @@ def run_serving(args, ws, rank, local):
         ok = ok and st == 0
         worst = max(worst, float(np.max(np.abs(w - p.lam))) / p.norm2)
     lat_ms = np.array(lat) * 1000.0
+    small_sel = np.array([sizes[s] <= 256 for s in sidx])
 
     # the plain one-at-a-time FP64 GPU path: one solve per size timed, then a
     # first-come-first-served queue of the same arrivals
@@ -730,6 +732,10 @@ def run_serving(args, ws, rank, local):
                 "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
                                "max": float(lat_ms.max()),
                                "library_p50": stats["p50_ms"], "library_p99": stats["p99_ms"]},
+                "latency_ms_by_class": {
+                    cls: {"count": int(sel.sum()), "p50": float(np.percentile(lat_ms[sel], 50)),
+                          "p99": float(np.percentile(lat_ms[sel], 99))}
+                    for cls, sel in (("n<=256", small_sel), ("n>256", ~small_sel)) if sel.any()},
                 "per_size_count": {str(m): int(np.sum(sidx == k)) for k, m in enumerate(sizes)},
                 "accuracy": {"max_rel_eig_err": worst, "ok_1e-13": worst <= 1e-13, "all_status_ok": ok},
                 "one_at_a_time_fp64": {"solves_per_s": count / (fin - t_arr[0]),
@@ -762,6 +768,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests of the stream to replay")
     args = ap.parse_args()
+    if args.workload == "serving":
+        # one hardware queue per serving lane (read when the CUDA context is created)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     ws, rank, local = dist_init()
     if args.workload == "product":
         run_product(args, ws, rank, local)

@@ -226,12 +226,26 @@ int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_of
  * Serving: continuous batching of eigenproblems of mixed sizes.  Requests
  * are admitted while their device footprint fits the memory budget and a
  * slot is free; admitted requests run concurrently on the device; finished
- * slots are recycled immediately for waiting requests.
+ * slots are recycled immediately for waiting requests.  Each slot has one
+ * stream; an eighth of them (at least one, from two slots up) run at the
+ * device's highest stream priority, the rest at its lowest.  Waiting
+ * requests of order <= 256 go first, as one micro-batch, preferably on a
+ * high-priority slot; otherwise the oldest larger request takes a
+ * low-priority slot alone.  Larger requests together hold at most 7/8 of
+ * the device's SMs, so small ones always find room, and the oldest larger
+ * request is passed over by at most four micro-batches.
+ * Streams beyond the CUDA_DEVICE_MAX_CONNECTIONS hardware queues (default
+ * 8) share a queue, where work runs in submission order and a micro-batch
+ * can wait behind another slot's large solve: set that variable to 32
+ * before the process's first CUDA call and keep max_slots <= 32.
+ * pjac_serve_create loads every kernel of the library on the current
+ * device (under lazy module loading a first launch would load it, and that
+ * load can wait for the solves already running).
  * ------------------------------------------------------------------- */
 typedef struct pjac_server pjac_server;
 
 typedef struct {
-    int max_slots;            /* concurrently admitted requests, 0: 64 */
+    int max_slots;            /* lanes (streams) running admitted work, <= 64; 0: 8 */
     int max_queue;            /* waiting (not yet admitted) requests, 0: 1 << 16 */
     size_t hbm_budget_bytes;  /* device bytes for admitted requests, 0: 8 GiB */
     pjac_opts solver;         /* options of every solve */

@@ -262,6 +262,16 @@ __global__ void __launch_bounds__(BT) b_precond_kernel(const BatchDesc* desc, in
     }
 }
 
+// Loads this file's kernels on the current device: asking for a kernel's
+// attributes loads it, where a first launch would otherwise do so later.
+cudaError_t preload_batched_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_diag32_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_precond_kernel);
+    return e;
+}
+
 }  // namespace pjac
 
 using namespace pjac;

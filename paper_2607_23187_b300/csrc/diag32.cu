@@ -432,4 +432,14 @@ cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* w
     return cudaLaunchCooperativeKernel((const void*)diag32_coop_kernel, dim3(grid), dim3(256), args, 0, st);
 }
 
+// Loads this file's kernels on the current device: asking for a kernel's
+// attributes loads it, where a first launch would otherwise do so later.
+cudaError_t preload_diag32_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, diag32_coop_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine32_coop_kernel);
+    return e;
+}
+
 }  // namespace pjac

@@ -221,4 +221,21 @@ cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cud
     return cudaGetLastError();
 }
 
+// Loads this file's kernels on the current device: asking for a kernel's
+// attributes loads it, where a first launch would otherwise do so later.
+cudaError_t preload_gemm_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, gemm_f64_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, symmetrize_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, copy_f32_f64_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, copy_f64_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, identity_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, round_fp32_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, add_f64_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, three_i_minus_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, check_finite_kernel);
+    return e;
+}
+
 }  // namespace pjac

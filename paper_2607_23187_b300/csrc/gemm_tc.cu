@@ -700,4 +700,17 @@ int gemm_split_bf16_launches(int m, int n, int k) {
     return 3 + (L.P.splits > 1 ? 1 : 0);
 }
 
+// Loads this file's kernels on the current device: asking for a kernel's
+// attributes loads it, where a first launch would otherwise do so later.
+cudaError_t preload_tc_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_rowmax_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_split_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_gemm_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_reduce_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_fold_status_kernel);
+    return e;
+}
+
 }  // namespace pjac

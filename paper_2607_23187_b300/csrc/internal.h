@@ -102,4 +102,11 @@ void handle_set_coop_cap(pjac_handle* h, int max_grid);
 cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st);
 cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st);
 
+// Kernel preloading (one function per source file), for the serving form.
+cudaError_t preload_batched_kernels();
+cudaError_t preload_diag32_kernels();
+cudaError_t preload_gemm_kernels();
+cudaError_t preload_tc_kernels();
+cudaError_t preload_jacobi_kernels();
+
 }  // namespace pjac

@@ -1299,4 +1299,21 @@ cudaError_t launch_info_batched(const BatchDesc* d_desc, int nb, pjac_info* info
     return cudaGetLastError();
 }
 
+// Loads this file's kernels on the current device: asking for a kernel's
+// attributes loads it, where a first launch would otherwise do so later.
+cudaError_t preload_jacobi_kernels() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, jacobi_single_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, jacobi_single_kernel<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, jacobi_batched_kernel<1>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, jacobi_batched_kernel<MAXR>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, rank_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, gather_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, readout_batched_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, info_batched_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, info_single_kernel);
+    return e;
+}
+
 }  // namespace pjac

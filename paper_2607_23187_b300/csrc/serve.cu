@@ -1,19 +1,35 @@
 // Serving form: continuous batching of eigenproblems of mixed orders.
 //
 // Requests arrive through pjac_serve_submit (host buffers).  The scheduler
-// (run from submit, poll and progress; no background thread) keeps a FIFO of
-// waiting requests and a set of lanes, each a CUDA stream with its own solver
-// handle.  A free lane takes work as soon as it appears:
-//   - requests of order <= BATCH_MAX_N waiting at that moment are admitted
-//     together as one micro-batch (the batched kernels, one persistent launch
-//     per stage), as many as the device-memory budget allows;
-//   - a larger request takes a lane alone and runs the single-problem path
-//     (cluster-parallel Jacobi).
+// (run from submit, poll and progress; no background thread) keeps two FIFOs
+// of waiting requests, small (order <= BATCH_MAX_N) and large, and a set of
+// lanes, each with its own solver handle and CUDA stream.  An eighth of the
+// lanes (at least one, from two lanes up) have a stream at the device's
+// highest priority, the others one at its lowest.  Whenever lanes are free:
+//   - small requests go first: every waiting small request that shares the
+//     oldest one's pivot rule and tolerance is admitted as one micro-batch
+//     (the batched kernels, one persistent launch per stage), preferably on
+//     a high-priority lane, as many as the device-memory budget allows;
+//   - otherwise the oldest large request takes a low-priority lane alone and
+//     runs the single-problem path (cluster-parallel Jacobi), provided the
+//     clusters of all running large requests still fit in the SMs outside a
+//     reserve of one eighth of the device.
+// One Jacobi CTA fills an SM's register file, so without the reserve the
+// large solves would hold every SM for seconds and a small request would wait
+// behind them; with it, small work always finds SMs, and the stream priority
+// puts its CTAs ahead of queued low-priority ones.  The oldest large request
+// is passed over by at most MAX_BYPASS micro-batches, so it cannot starve.
+// Streams beyond CUDA_DEVICE_MAX_CONNECTIONS share hardware queues, in which
+// work runs in submission order: a micro-batch could then wait behind a
+// large solve of another lane.  Hence one stream per lane, and the advice to
+// raise that limit to 32 and keep max_slots <= 32.
+// Creating a server loads all kernels of the library on the current device,
+// so that no first-launch load happens while requests run.
 // Admission is by device footprint: a request is admitted only while the
-// bytes of all admitted requests stay within the budget.  Work of different
-// lanes overlaps on the device.  A lane's results are copied back on its
-// stream; completion is detected with an event query, and the lane is
-// recycled at once.  Latency = completion detected - submit.
+// bytes of all admitted requests stay within the budget (one request is
+// always admitted).  A lane's results are copied back on its stream;
+// completion is detected with an event query, and the lane is recycled at
+// once.  Latency = completion detected - submit.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -35,6 +51,7 @@ using namespace pjac;
 namespace {
 
 constexpr int BATCH_MAX_N = 256;
+constexpr int MAX_BYPASS = 4;
 using clk = std::chrono::steady_clock;
 
 double now_ms() {
@@ -55,10 +72,13 @@ struct Request {
     int status = PJAC_PENDING;
     pjac_info info;
     size_t footprint;
+    int bypassed = 0;            // micro-batches admitted ahead of it while it could have run
 };
 
 struct Lane {
     cudaStream_t st = nullptr;
+    bool hi = false;                 // high-priority stream: micro-batches only
+    int sms = 0;                     // SMs held by the current large request, 0 for a micro-batch
     pjac_handle* h = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
@@ -128,7 +148,9 @@ struct pjac_server {
     pjac_serve_opts o;
     std::mutex mu;
     std::vector<Lane> lanes;
-    std::deque<Request*> queue;
+    std::deque<Request*> q_small, q_large;       // waiting requests, oldest first
+    int large_sms = 0;                           // SMs held by running large requests
+    int large_sms_cap = 0;                       // SMs large requests may hold together
     std::unordered_map<uint64_t, Request*> all;   // queued, running or finished-not-polled
     uint64_t next_ticket = 1;
     size_t in_use = 0;
@@ -161,13 +183,36 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
     if (d.max_slots > 64) return set_err(PJAC_EINVAL, "max_slots must be <= 64");
     auto* sv = new pjac_server();
     sv->o = d;
+    int dev = 0, sms = 0, prio_lo = 0, prio_hi = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+        cudaSuccess || cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        delete sv;
+        return set_err(PJAC_ECUDA, "serve: device query failed");
+    }
+    sv->large_sms_cap = sms - sms / 8;
+    // Load every kernel now: under lazy module loading a kernel's first
+    // launch loads it, and the load can wait for work already running on the
+    // device, which would stall the scheduler behind seconds-long solves.
+    cudaError_t el = preload_batched_kernels();
+    if (el == cudaSuccess) el = preload_diag32_kernels();
+    if (el == cudaSuccess) el = preload_gemm_kernels();
+    if (el == cudaSuccess) el = preload_tc_kernels();
+    if (el == cudaSuccess) el = preload_jacobi_kernels();
+    if (el != cudaSuccess) {
+        delete sv;
+        return cuda_err(el, "serve: loading the kernels");
+    }
     sv->lanes.resize(d.max_slots);
-    for (auto& L : sv->lanes) {
+    int n_hi = d.max_slots >= 2 ? std::max(1, d.max_slots / 8) : 0;
+    for (int li = 0; li < d.max_slots; ++li) {
+        Lane& L = sv->lanes[li];
+        L.hi = li < n_hi;
         int r = pjac_create(&L.h, &d.solver);
         // a served request's preconditioner must start beside running solves:
         // its cooperative kernels use at most 64 CTAs instead of the whole GPU
         if (r == PJAC_OK) handle_set_coop_cap(L.h, 64);
-        cudaError_t e1 = cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking);
+        cudaError_t e1 = cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, L.hi ? prio_hi : prio_lo);
         cudaError_t e2 = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
         if (r != PJAC_OK || e1 != cudaSuccess || e2 != cudaSuccess) {
             pjac_serve_destroy(sv);
@@ -264,8 +309,59 @@ static void finish_lane(pjac_server* s, Lane& L, int launch_err) {
         s->inflight--;
         s->in_use -= q->footprint;
     }
+    s->large_sms -= L.sms;
+    L.sms = 0;
     L.reqs.clear();
     L.busy = false;
+}
+
+// Admits the next piece of work onto a free lane (see the header comment);
+// returns that lane, or nullptr when nothing can be admitted now.
+static Lane* admit(pjac_server* s) {
+    Lane* free_hi = nullptr;
+    Lane* free_lo = nullptr;
+    for (auto& L : s->lanes) {
+        if (L.busy) continue;
+        if (L.hi && !free_hi) free_hi = &L;
+        if (!L.hi && !free_lo) free_lo = &L;
+    }
+    if (!free_hi && !free_lo) return nullptr;
+    size_t budget = s->o.hbm_budget_bytes - std::min(s->o.hbm_budget_bytes, s->in_use);
+    Request* big = s->q_large.empty() ? nullptr : s->q_large.front();
+    Request* small = s->q_small.empty() ? nullptr : s->q_small.front();
+    int P = 0;
+    bool big_ok = false;
+    if (big && free_lo) {
+        P = s->o.solver.cluster_size > 0 ? s->o.solver.cluster_size : jacobi_auto_cluster(big->n);
+        big_ok = (big->footprint <= budget || s->in_use == 0) &&
+                 (s->large_sms == 0 || s->large_sms + P <= s->large_sms_cap);
+    }
+    bool small_ok = small && (small->footprint <= budget || s->in_use == 0);
+    if (small_ok && !(big_ok && big->bypassed >= MAX_BYPASS)) {
+        Lane& L = free_hi ? *free_hi : *free_lo;
+        size_t used = 0;
+        for (auto it = s->q_small.begin(); it != s->q_small.end();) {
+            Request* q = *it;
+            if (q->pivot == small->pivot && q->tol == small->tol &&
+                (used + q->footprint <= budget || L.reqs.empty()) && L.reqs.size() < 4096) {
+                used += q->footprint;
+                L.reqs.push_back(q);
+                it = s->q_small.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        if (big_ok) big->bypassed++;
+        L.sms = 0;
+        return &L;
+    }
+    if (!big_ok) return nullptr;
+    Lane& L = *free_lo;
+    s->q_large.pop_front();
+    L.reqs.push_back(big);
+    L.sms = P;
+    s->large_sms += P;
+    return &L;
 }
 
 // One scheduling pass: retire finished lanes, then admit waiting requests.
@@ -276,29 +372,8 @@ static void schedule(pjac_server* s) {
         if (e == cudaSuccess) finish_lane(s, L, PJAC_OK);
         else if (e != cudaErrorNotReady) { cudaGetLastError(); finish_lane(s, L, PJAC_ECUDA); }
     }
-    for (auto& L : s->lanes) {
-        if (L.busy || s->queue.empty()) continue;
-        Request* head = s->queue.front();
-        if (s->in_use + head->footprint > s->o.hbm_budget_bytes && s->in_use > 0) break;
-        if (head->n > BATCH_MAX_N) {
-            s->queue.pop_front();
-            L.reqs.push_back(head);
-        } else {
-            // micro-batch: every waiting small request with the head's pivot and tol, within budget
-            size_t budget = s->o.hbm_budget_bytes - std::min(s->o.hbm_budget_bytes, s->in_use);
-            size_t used = 0;
-            for (auto it = s->queue.begin(); it != s->queue.end();) {
-                Request* q = *it;
-                if (q->n <= BATCH_MAX_N && q->pivot == head->pivot && q->tol == head->tol &&
-                    (used + q->footprint <= budget || L.reqs.empty()) && L.reqs.size() < 4096) {
-                    used += q->footprint;
-                    L.reqs.push_back(q);
-                    it = s->queue.erase(it);
-                } else {
-                    ++it;
-                }
-            }
-        }
+    while (Lane* lp = admit(s)) {
+        Lane& L = *lp;
         for (Request* q : L.reqs) {
             s->in_use += q->footprint;
             s->inflight++;
@@ -319,7 +394,8 @@ extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda
     if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     std::lock_guard<std::mutex> lk(s->mu);
-    if ((int)s->queue.size() >= s->o.max_queue) return set_err(PJAC_EAGAIN, "serve: queue full");
+    if ((int)(s->q_small.size() + s->q_large.size()) >= s->o.max_queue)
+        return set_err(PJAC_EAGAIN, "serve: queue full");
     for (int c = 0; c < n; ++c)
         for (int r = 0; r < n; ++r) {
             double v = A[r + (size_t)c * lda];
@@ -339,7 +415,7 @@ extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda
     q->t_submit = now_ms();
     q->footprint = request_footprint(n);
     if (s->first_submit < 0) s->first_submit = q->t_submit;
-    s->queue.push_back(q);
+    (n <= BATCH_MAX_N ? s->q_small : s->q_large).push_back(q);
     s->all[q->ticket] = q;
     *ticket = q->ticket;
     schedule(s);
@@ -365,7 +441,7 @@ extern "C" int pjac_serve_progress(pjac_server* s) {
     if (!s) return set_err(PJAC_EINVAL, "NULL server");
     std::lock_guard<std::mutex> lk(s->mu);
     schedule(s);
-    return (int)(s->queue.size() + s->inflight);
+    return (int)(s->q_small.size() + s->q_large.size() + s->inflight);
 }
 
 extern "C" int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st) {

@@ -7,7 +7,9 @@ bit for bit against the oracle with one CTA).  Here:
     (|dlambda| <= 1e-13 ||A||_2, residual and orthogonality <= 1e-12);
   * a problem's result does not depend on the batch it is solved in
     (bit-identical alone and inside a batch of mixed sizes);
-  * a served request gives the same result alone and in a mixed stream.
+  * a served request gives the same result alone and in a mixed stream;
+  * the serving scheduler runs waiting small requests ahead of a waiting
+    large one, at most four micro-batches in a row.
 """
 import time
 
@@ -121,3 +123,37 @@ def test_serving_admission_and_errors(pj):
     with pytest.raises(pj.PjacError):
         srv.submit(bad)
     srv.close()
+
+
+def test_serving_small_first_with_bounded_bypass(pj):
+    """One lane, so the completion order is the run order.  A large request
+    A takes the lane at once; then a large L and six small requests wait,
+    the small ones with distinct tolerances (so each is its own
+    micro-batch).  The small ones run first, but L is passed over by at
+    most four micro-batches: A, S1..S4, L, S5, S6."""
+    rng = np.random.default_rng(9)
+    pa = pin.small_clustered_problem(400, rng, "clustered")
+    pl = pin.small_clustered_problem(300, rng, "clustered")
+    ps = [pin.small_clustered_problem(64 + 16 * k, rng, "uniform") for k in range(6)]
+    srv = pj.Server(max_slots=1)
+    names = ["A", "L"] + ["S%d" % (k + 1) for k in range(6)]
+    probs = [pa, pl] + ps
+    tols = [1e-15, 1e-15] + [(k + 1) * 1e-15 for k in range(6)]
+    tickets = [srv.submit(p.a, "gap", t) for p, t in zip(probs, tols)]
+    order, res = [], {}
+    t0 = time.time()
+    while len(order) < len(tickets) and time.time() - t0 < 300.0:
+        for name, t in zip(names, tickets):
+            if name in res:
+                continue
+            st, info, w, v = srv.poll(t)
+            if st == pj.PJAC_PENDING:
+                continue
+            res[name] = (st, w.copy(), v.copy())
+            order.append(name)
+        time.sleep(0.001)
+    srv.close()
+    assert order == ["A", "S1", "S2", "S3", "S4", "L", "S5", "S6"]
+    for name, p in zip(names, probs):
+        assert res[name][0] == 0
+        _check(p, res[name][1], res[name][2])
