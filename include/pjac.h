@@ -284,6 +284,7 @@ typedef struct {
     double solves_per_s;      /* completed / (last completion - first submission) */
     int64_t peak_inflight;
     size_t peak_hbm_bytes;
+    int64_t launches;         /* kernel launches of this library enqueued so far */
 } pjac_serve_stats;
 int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
 
@@ -292,6 +293,13 @@ int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
  * element-wise steps, the Jacobi kernel, the readout).  A diagnostic for
  * launch accounting; returns -1 when h is NULL or n is out of range. */
 int pjac_solve_launch_count(pjac_handle* h, int n);
+
+/* Number of kernel launches of this library that one pjac_product of shape
+ * m x n x k makes with the handle's current transform (split BF16: digit
+ * split, slice products, reduction when the inner dimension is split; FP64:
+ * one).  Returns -1 when h is NULL, a size is out of range, or the split
+ * product does not support the shape. */
+int pjac_product_launch_count(pjac_handle* h, int m, int n, int k);
 
 /* Human-readable text for a status code (static storage). */
 const char* pjac_status_string(int status);

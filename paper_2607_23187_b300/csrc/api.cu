@@ -538,6 +538,13 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     return c;
 }
 
+extern "C" int pjac_product_launch_count(pjac_handle* h, int m, int n, int k) {
+    if (!h || m < 1 || n < 1 || k < 1 || m > PJAC_MAX_N || n > PJAC_MAX_N || k > PJAC_MAX_N) return -1;
+    if (h->opts.transform != PJAC_TRANSFORM_SPLIT_BF16) return 1;
+    int c = gemm_split_bf16_launches(m, n, k);
+    return c > 0 ? c : -1;
+}
+
 extern "C" const char* pjac_status_string(int s) {
     switch (s) {
         case PJAC_OK: return "PJAC_OK";

@@ -109,4 +109,6 @@ cudaError_t preload_gemm_kernels();
 cudaError_t preload_tc_kernels();
 cudaError_t preload_jacobi_kernels();
 
+int batched_launch_count();
+
 }  // namespace pjac

@@ -156,6 +156,7 @@ struct pjac_server {
     size_t in_use = 0;
     int64_t inflight = 0, peak_inflight = 0;
     size_t peak_hbm = 0;
+    int64_t launches = 0;                        // kernel launches of this library enqueued so far
     std::vector<double> lat_ms;
     double first_submit = -1, last_done = -1;
 };
@@ -272,9 +273,13 @@ static int launch_lane(pjac_server* s, Lane& L) {
     if (batched) {
         r = pjac_solve_batched(L.h, nb, L.ns.data(), L.aoff.data(), L.dA, L.woff.data(), L.dW, L.aoff.data(),
                                L.dV, r0->pivot, r0->tol, L.dInfo, L.st);
+        if (r == PJAC_OK) s->launches += batched_launch_count();
     } else {
         // single large request: asynchronous single-problem path
         r = solve_async_dev(L.h, L.dA, r0->n, r0->n, r0->pivot, r0->tol, L.dW, L.dV, r0->n, L.dInfo, L.st);
+        // as many as pjac_solve: no device input check (the host checked at
+        // submission), one kernel more to copy the report
+        if (r == PJAC_OK) s->launches += pjac_solve_launch_count(L.h, r0->n);
     }
     if (r != PJAC_OK) return r;
     e = cudaMemcpyAsync(L.hW, L.dW, totW * 8, cudaMemcpyDeviceToHost, L.st);
@@ -452,6 +457,7 @@ extern "C" int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st) {
     st->completed = (int64_t)v.size();
     st->peak_inflight = s->peak_inflight;
     st->peak_hbm_bytes = s->peak_hbm;
+    st->launches = s->launches;
     if (v.empty()) return PJAC_OK;
     std::sort(v.begin(), v.end());
     auto pct = [&](double p) {

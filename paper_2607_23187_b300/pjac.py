@@ -33,6 +33,7 @@ EXPORTS = (
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
     "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
+    "pjac_product_launch_count",
 )
 
 
@@ -69,7 +70,8 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("solves_per_s", ctypes.c_double),
-                ("peak_inflight", ctypes.c_int64), ("peak_hbm_bytes", ctypes.c_size_t)]
+                ("peak_inflight", ctypes.c_int64), ("peak_hbm_bytes", ctypes.c_size_t),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -109,6 +111,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_serve_progress.argtypes = [vp]
         L.pjac_serve_get_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
         L.pjac_solve_launch_count.argtypes = [vp, i]
+        L.pjac_product_launch_count.argtypes = [vp, i, i, i]
         L.pjac_status_string.argtypes = [i]
         L.pjac_status_string.restype = ctypes.c_char_p
         L.pjac_last_error.argtypes = []

@@ -152,8 +152,14 @@ def test_serving_small_first_with_bounded_bypass(pj):
             res[name] = (st, w.copy(), v.copy())
             order.append(name)
         time.sleep(0.001)
+    launches = srv.stats()["launches"]
     srv.close()
     assert order == ["A", "S1", "S2", "S3", "S4", "L", "S5", "S6"]
+    # two single-problem pipelines and six micro-batches of five kernels
+    h = pj.Handle()
+    count = pj.load().pjac_solve_launch_count
+    assert launches == count(h.h, 400) + count(h.h, 300) + 6 * 5
+    h.close()
     for name, p in zip(names, probs):
         assert res[name][0] == 0
         _check(p, res[name][1], res[name][2])

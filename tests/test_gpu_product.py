@@ -159,6 +159,15 @@ def test_bad_arguments(pj, h):
     assert lib.pjac_product(h.h, 0, 0, 4, 4, 4, 1.0, None, 4, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
 
 
+def test_launch_count(pj, h):
+    lib = pj.load()
+    assert lib.pjac_product_launch_count(h.h, 1000, 900, 800) in (3, 4)
+    assert lib.pjac_product_launch_count(h.h, 0, 4, 4) == -1
+    assert lib.pjac_product_launch_count(None, 4, 4, 4) == -1
+    with pj.Handle(transform="fp64") as h64:
+        assert lib.pjac_product_launch_count(h64.h, 1000, 900, 800) == 1
+
+
 def test_preconditioner_with_split_product(pj, h):
     """Sec. 2.1 with the tensor-core products: same Q0, the A1 of the split
     product and of the FP64 product agree to the transform's error, and
