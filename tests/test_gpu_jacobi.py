@@ -123,6 +123,35 @@ def test_cluster_parity_n520(pj, h, pivot, cluster):
     assert np.max(np.abs(gw - p.lam)) <= 1e-13 * p.norm2
 
 
+def ties_matrix(kind, n):
+    """Matrices whose scores tie exactly, so that the tie rule (smallest
+    (i, j)) and the exact evaluation of near-equal keys decide the pivots:
+    equal off-diagonals over an equal diagonal (every initial score equal),
+    small integers (many equal |a_ij| and equal gaps), and the constant
+    tridiagonal (every nonzero score equal at the start)."""
+    if kind == "equal":
+        return 2.0 * np.eye(n) + 0.5 * (np.ones((n, n)) - np.eye(n))
+    if kind == "int":
+        rng = np.random.default_rng(17)
+        u = np.triu(rng.integers(-2, 3, size=(n, n)).astype(np.float64), 1)
+        return u + u.T + np.diag(rng.integers(-3, 4, size=n).astype(np.float64))
+    a = np.zeros((n, n))
+    i = np.arange(n - 1)
+    a[i, i + 1] = a[i + 1, i] = 1.0
+    return a
+
+
+@pytest.mark.parametrize("pivot", ["gap", "greedy"])
+@pytest.mark.parametrize("kind,n,cluster", [("equal", 70, 1), ("equal", 70, 2), ("int", 130, 1),
+                                            ("int", 130, 4), ("tridiag", 130, 2)])
+def test_exact_ties_parity(pj, h, kind, n, cluster, pivot):
+    a = ties_matrix(kind, n)
+    r, w, v = oracle_run(("ties", kind, n), a, None, pivot, 1e-15)
+    gw, gv, ga, info, st = gpu_run(pj, h, a, None, pivot, 1e-15, cluster_size=cluster)
+    assert st == 0 and r["status"] == 0
+    assert_bit_parity(r, w, v, gw, gv, ga, info)
+
+
 def test_cyclic_cluster_parity(pj, h):
     p, q0, q, a1 = preconditioned("cfg2", n=200)
     r, w, v = oracle_run("cfg2_200", a1, q, "cyclic", 1e-15)
