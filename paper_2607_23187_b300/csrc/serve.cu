@@ -1,35 +1,29 @@
 // Serving form: continuous batching of eigenproblems of mixed orders.
 //
 // Requests arrive through pjac_serve_submit (host buffers).  The scheduler
-// (run from submit, poll and progress; no background thread) keeps two FIFOs
-// of waiting requests, small (order <= BATCH_MAX_N) and large, and a set of
-// lanes, each with its own solver handle and CUDA stream.  An eighth of the
+// runs from submit, poll and progress (no background thread).  Its admission
+// policy (serve_sched.h): small requests (order <= 256) first, as
+// micro-batches on the batched kernels; otherwise the oldest large request
+// alone on the single-problem path (cluster-parallel Jacobi), while the SMs
+// of all running large requests fit outside a reserve of one eighth of the
+// device; the oldest large request is passed over by at most four
+// micro-batches.
+// Each lane has its own solver handle and one CUDA stream.  An eighth of the
 // lanes (at least one, from two lanes up) have a stream at the device's
-// highest priority, the others one at its lowest.  Whenever lanes are free:
-//   - small requests go first: every waiting small request that shares the
-//     oldest one's pivot rule and tolerance is admitted as one micro-batch
-//     (the batched kernels, one persistent launch per stage), preferably on
-//     a high-priority lane, as many as the device-memory budget allows;
-//   - otherwise the oldest large request takes a low-priority lane alone and
-//     runs the single-problem path (cluster-parallel Jacobi), provided the
-//     clusters of all running large requests still fit in the SMs outside a
-//     reserve of one eighth of the device.
-// One Jacobi CTA fills an SM's register file, so without the reserve the
-// large solves would hold every SM for seconds and a small request would wait
-// behind them; with it, small work always finds SMs, and the stream priority
-// puts its CTAs ahead of queued low-priority ones.  The oldest large request
-// is passed over by at most MAX_BYPASS micro-batches, so it cannot starve.
+// highest priority and take micro-batches first; the others have one at its
+// lowest.  One Jacobi CTA fills an SM's register file, so without the
+// reserve the large solves would hold every SM for seconds and a small
+// request would wait behind them; with it, small work always finds SMs, and
+// the stream priority puts its CTAs ahead of queued low-priority ones.
 // Streams beyond CUDA_DEVICE_MAX_CONNECTIONS share hardware queues, in which
 // work runs in submission order: a micro-batch could then wait behind a
 // large solve of another lane.  Hence one stream per lane, and the advice to
 // raise that limit to 32 and keep max_slots <= 32.
 // Creating a server loads all kernels of the library on the current device,
 // so that no first-launch load happens while requests run.
-// Admission is by device footprint: a request is admitted only while the
-// bytes of all admitted requests stay within the budget (one request is
-// always admitted).  A lane's results are copied back on its stream;
-// completion is detected with an event query, and the lane is recycled at
-// once.  Latency = completion detected - submit.
+// A lane's results are copied back on its stream; completion is detected
+// with an event query, and the lane is recycled at once.
+// Latency = completion detected - submit.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -41,6 +35,7 @@
 #include <unordered_map>
 #include <vector>
 #include "internal.h"
+#include "serve_sched.h"
 
 namespace pjac {
 int set_err(int code, const char* fmt, ...);
@@ -50,8 +45,6 @@ using namespace pjac;
 
 namespace {
 
-constexpr int BATCH_MAX_N = 256;
-constexpr int MAX_BYPASS = 4;
 using clk = std::chrono::steady_clock;
 
 double now_ms() {
@@ -148,12 +141,9 @@ struct pjac_server {
     pjac_serve_opts o;
     std::mutex mu;
     std::vector<Lane> lanes;
-    std::deque<Request*> q_small, q_large;       // waiting requests, oldest first
-    int large_sms = 0;                           // SMs held by running large requests
-    int large_sms_cap = 0;                       // SMs large requests may hold together
+    ServeQueue<Request> q;                       // waiting requests, admitted bytes and SMs
     std::unordered_map<uint64_t, Request*> all;   // queued, running or finished-not-polled
     uint64_t next_ticket = 1;
-    size_t in_use = 0;
     int64_t inflight = 0, peak_inflight = 0;
     size_t peak_hbm = 0;
     int64_t launches = 0;                        // kernel launches of this library enqueued so far
@@ -191,7 +181,8 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
         delete sv;
         return set_err(PJAC_ECUDA, "serve: device query failed");
     }
-    sv->large_sms_cap = sms - sms / 8;
+    sv->q.sms_cap = sms - sms / 8;
+    sv->q.budget = d.hbm_budget_bytes;
     // Load every kernel now: under lazy module loading a kernel's first
     // launch loads it, and the load can wait for work already running on the
     // device, which would stall the scheduler behind seconds-long solves.
@@ -269,7 +260,7 @@ static int launch_lane(pjac_server* s, Lane& L) {
     cudaError_t e = cudaMemcpyAsync(L.dA, L.hA, totA * 8, cudaMemcpyHostToDevice, L.st);
     if (e != cudaSuccess) return cuda_err(e, "serve H2D");
     Request* r0 = L.reqs[0];
-    bool batched = r0->n <= BATCH_MAX_N;
+    bool batched = r0->n <= SERVE_BATCH_MAX_N;
     if (batched) {
         r = pjac_solve_batched(L.h, nb, L.ns.data(), L.aoff.data(), L.dA, L.woff.data(), L.dW, L.aoff.data(),
                                L.dV, r0->pivot, r0->tol, L.dInfo, L.st);
@@ -312,61 +303,10 @@ static void finish_lane(pjac_server* s, Lane& L, int launch_err) {
         s->lat_ms.push_back(t - q->t_submit);
         s->last_done = t;
         s->inflight--;
-        s->in_use -= q->footprint;
     }
-    s->large_sms -= L.sms;
-    L.sms = 0;
+    serve_release(s->q, L);
     L.reqs.clear();
     L.busy = false;
-}
-
-// Admits the next piece of work onto a free lane (see the header comment);
-// returns that lane, or nullptr when nothing can be admitted now.
-static Lane* admit(pjac_server* s) {
-    Lane* free_hi = nullptr;
-    Lane* free_lo = nullptr;
-    for (auto& L : s->lanes) {
-        if (L.busy) continue;
-        if (L.hi && !free_hi) free_hi = &L;
-        if (!L.hi && !free_lo) free_lo = &L;
-    }
-    if (!free_hi && !free_lo) return nullptr;
-    size_t budget = s->o.hbm_budget_bytes - std::min(s->o.hbm_budget_bytes, s->in_use);
-    Request* big = s->q_large.empty() ? nullptr : s->q_large.front();
-    Request* small = s->q_small.empty() ? nullptr : s->q_small.front();
-    int P = 0;
-    bool big_ok = false;
-    if (big && free_lo) {
-        P = s->o.solver.cluster_size > 0 ? s->o.solver.cluster_size : jacobi_auto_cluster(big->n);
-        big_ok = (big->footprint <= budget || s->in_use == 0) &&
-                 (s->large_sms == 0 || s->large_sms + P <= s->large_sms_cap);
-    }
-    bool small_ok = small && (small->footprint <= budget || s->in_use == 0);
-    if (small_ok && !(big_ok && big->bypassed >= MAX_BYPASS)) {
-        Lane& L = free_hi ? *free_hi : *free_lo;
-        size_t used = 0;
-        for (auto it = s->q_small.begin(); it != s->q_small.end();) {
-            Request* q = *it;
-            if (q->pivot == small->pivot && q->tol == small->tol &&
-                (used + q->footprint <= budget || L.reqs.empty()) && L.reqs.size() < 4096) {
-                used += q->footprint;
-                L.reqs.push_back(q);
-                it = s->q_small.erase(it);
-            } else {
-                ++it;
-            }
-        }
-        if (big_ok) big->bypassed++;
-        L.sms = 0;
-        return &L;
-    }
-    if (!big_ok) return nullptr;
-    Lane& L = *free_lo;
-    s->q_large.pop_front();
-    L.reqs.push_back(big);
-    L.sms = P;
-    s->large_sms += P;
-    return &L;
 }
 
 // One scheduling pass: retire finished lanes, then admit waiting requests.
@@ -377,14 +317,13 @@ static void schedule(pjac_server* s) {
         if (e == cudaSuccess) finish_lane(s, L, PJAC_OK);
         else if (e != cudaErrorNotReady) { cudaGetLastError(); finish_lane(s, L, PJAC_ECUDA); }
     }
-    while (Lane* lp = admit(s)) {
+    const int cluster = s->o.solver.cluster_size;
+    auto sms_of = [cluster](int n) { return cluster > 0 ? cluster : jacobi_auto_cluster(n); };
+    while (Lane* lp = serve_admit(s->q, s->lanes, sms_of)) {
         Lane& L = *lp;
-        for (Request* q : L.reqs) {
-            s->in_use += q->footprint;
-            s->inflight++;
-        }
+        s->inflight += (int64_t)L.reqs.size();
         s->peak_inflight = std::max(s->peak_inflight, s->inflight);
-        s->peak_hbm = std::max(s->peak_hbm, s->in_use);
+        s->peak_hbm = std::max(s->peak_hbm, s->q.in_use);
         L.busy = true;
         int r = launch_lane(s, L);
         if (r != PJAC_OK) finish_lane(s, L, r);
@@ -399,7 +338,7 @@ extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda
     if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     std::lock_guard<std::mutex> lk(s->mu);
-    if ((int)(s->q_small.size() + s->q_large.size()) >= s->o.max_queue)
+    if ((int)s->q.waiting() >= s->o.max_queue)
         return set_err(PJAC_EAGAIN, "serve: queue full");
     for (int c = 0; c < n; ++c)
         for (int r = 0; r < n; ++r) {
@@ -420,7 +359,7 @@ extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda
     q->t_submit = now_ms();
     q->footprint = request_footprint(n);
     if (s->first_submit < 0) s->first_submit = q->t_submit;
-    (n <= BATCH_MAX_N ? s->q_small : s->q_large).push_back(q);
+    s->q.push(q);
     s->all[q->ticket] = q;
     *ticket = q->ticket;
     schedule(s);
@@ -446,7 +385,7 @@ extern "C" int pjac_serve_progress(pjac_server* s) {
     if (!s) return set_err(PJAC_EINVAL, "NULL server");
     std::lock_guard<std::mutex> lk(s->mu);
     schedule(s);
-    return (int)(s->q_small.size() + s->q_large.size() + s->inflight);
+    return (int)(s->q.waiting() + s->inflight);
 }
 
 extern "C" int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st) {
