@@ -10,8 +10,8 @@
 // micro-batches.
 // Each lane has its own solver handle and one CUDA stream.  An eighth of the
 // lanes (at least one, from two lanes up) have a stream at the device's
-// highest priority and take micro-batches first; the others have one at its
-// lowest.  One Jacobi CTA fills an SM's register file, so without the
+// highest priority and take only micro-batches, which go to them first; the
+// others have one at its lowest.  One Jacobi CTA fills an SM's register file, so without the
 // reserve the large solves would hold every SM for seconds and a small
 // request would wait behind them; with it, small work always finds SMs, and
 // the stream priority puts its CTAs ahead of queued low-priority ones.
