@@ -92,6 +92,38 @@ __device__ __forceinline__ Eval eval_pair(double dii, double djj, double q) {
     return r;
 }
 
+// The same evaluation in two halves, so that the score can be published
+// before the cosine is known: the head gives l and t (as eval_pair) and the
+// scaled den and 4q^2; rot_cs then gives c and s from them, bit for bit as
+// eval_pair (c is a ratio of scaled quantities, so the scaling drops out).
+struct EvalHead { double l, t, den, q4; };
+
+__device__ __forceinline__ EvalHead eval_pair_head(double dii, double djj, double q) {
+    EvalHead r;
+    if (q == 0.0) { r.l = 0.0; r.t = 0.0; r.den = 1.0; r.q4 = 0.0; return r; }   // rot_cs: c = 1, s = 0
+    double d = __dadd_rn(dii, -djj);
+    int e = scale_exp(d, q);
+    if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
+    double q2 = __dmul_rn(q, q);
+    double q4 = __dmul_rn(4.0, q2);
+    double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(d, d), q4));
+    double den = __dadd_rn(fabs(d), rr);
+    double l = __ddiv_rn(__dmul_rn(2.0, q2), den);
+    if (e != 0) l = ldexp(l, e);
+    double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
+    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    r.l = l;
+    r.t = t;
+    r.den = den;
+    r.q4 = q4;
+    return r;
+}
+
+__device__ __forceinline__ void rot_cs(double den, double q4, double t, double& c, double& s) {
+    c = __ddiv_rn(den, __dsqrt_rn(__dadd_rn(__dmul_rn(den, den), q4)));
+    s = __dmul_rn(t, c);
+}
+
 // ---------------------------------------------------------------------------
 // Screen keys.  Selecting the pivot needs the exact argmax of the FP64
 // scores (ties to the smallest index), but an FP64 square root and division

@@ -55,7 +55,7 @@ struct Cand {
 struct Slot {
     Cand loc, pi, pj;       // this CTA's best own row, its part of row i, of row j
     int ki[2], kj[2];       // the two largest keys of its parts of rows i and j
-    double prm[3][3];       // (c, s, t) of the rotation of each of the three
+    double prm[3][3];       // (den, 4q^2, t) of each candidate's rotation (scaled; rot_cs gives c, s)
     double sum;
     int flags, pad;
 };
@@ -74,11 +74,16 @@ struct Sh {
     Cand sel;
     int tflag, pad3;
     double c, s, t, dii, djj, q;
+    double cs[48][2];       // (c, s) of every published candidate (3 per cluster rank)
     double old_di, old_dj;  // diagonal entries before the pending rotation
     double normf, thr, eps_li, scale;
     int pi, pj, nresc, decision;
+    int win, pad4;          // inbox index of the pending pivot
     int key_eps, pad2;
 };
+
+// warps 3 and up finish (c, s) of the 3 candidates of each of up to 16 ranks
+static_assert((NT / 32 - 3) * 32 >= 48, "too few warps for the cosines of the published candidates");
 
 #ifdef PJAC_PROFILE
 // Profiling build only: per-phase clock totals of CTA 0 and event counts.
@@ -802,30 +807,33 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         int pdec = 1, ppi = 0, ppj = 0;
         double pend_c = 1.0, pend_s = 0.0;
         // Publish this CTA's three candidates (best own row, its part of row
-        // i, its part of row j) with their exact scores and rotations --
+        // i, its part of row j) with their exact scores and tangents --
         // evaluated by three lanes at once, from one shared denominator --
         // push them into every rank's inbox, and select after the cluster
-        // barrier.  Every CTA ends with the same winner in sh.sel and its
-        // rotation in sh.c, sh.s, sh.t; the owners of rows i and j take
-        // those rows' new bests.  i, j < 0: no rows i, j (first selection).
+        // barrier.  The cosines and sines are not on the path to the
+        // decision: after the barrier, while warp 0 decides, warps 3 and up
+        // finish them for every published candidate.  Every CTA ends with
+        // the same winner in sh.sel and its rotation in pend_c, pend_s and
+        // sh.t; the owners of rows i and j take those rows' new bests.
+        // i, j < 0: no rows i, j (first selection).
         auto publish_select = [&](Cand loc, Cand pI, Cand pJ, const int (&kI)[2], const int (&kJ)[2], int i,
                                   int j) {
             if (tid < 3) {
                 Cand c = (tid == 0) ? loc : (tid == 1 ? pI : pJ);
-                double rc = 1.0, rs = 0.0, rt = 0.0;
+                double rd = 1.0, rq = 0.0, rt = 0.0;   // rot_cs: c = 1, s = 0
                 if (c.key != KEY_NONE) {
                     int ci = min(c.row, c.col), cj = max(c.row, c.col);
-                    Eval ev = eval_pair(diag[ci], diag[cj], c.x);
+                    EvalHead ev = eval_pair_head(diag[ci], diag[cj], c.x);
                     if (pivot != PJAC_PIVOT_GREEDY) c.ex = ev.l;
-                    rc = ev.c;
-                    rs = ev.s;
+                    rd = ev.den;
+                    rq = ev.q4;
                     rt = ev.t;
                 }
                 if (tid == 0) sh.stage.loc = c;
                 else if (tid == 1) sh.stage.pi = c;
                 else sh.stage.pj = c;
-                sh.stage.prm[tid][0] = rc;
-                sh.stage.prm[tid][1] = rs;
+                sh.stage.prm[tid][0] = rd;
+                sh.stage.prm[tid][1] = rq;
                 sh.stage.prm[tid][2] = rt;
                 if (tid == 0) {
                     sh.stage.sum = 0.0; sh.stage.flags = sh.tflag; sh.stage.pad = 0;
@@ -885,8 +893,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                         const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
                         sh.pi = i2;
                         sh.pj = j2;
-                        sh.c = pr[0];
-                        sh.s = pr[1];
+                        sh.win = g.pad;
                         sh.t = pr[2];
                         // the pending rotation's diagonal, undone if the
                         // convergence test stops before the rotation
@@ -917,14 +924,23 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     cache2[row - k0] = no_cand();
                     cachef[row - k0] = bound_without_head(c, ka, kb);
                 }
+            } else if (warp >= 3) {
+                // cosine and sine of every published candidate's rotation
+                const int e = (warp - 3) * 32 + lane;
+                if (e < 3 * P) {
+                    const double* pr = sh.inbox[par][e / 3].prm[e % 3];
+                    rot_cs(pr[0], pr[1], pr[2], sh.cs[e][0], sh.cs[e][1]);
+                }
             }
             par ^= 1;
             __syncthreads();
             pdec = sh.decision;
             ppi = sh.pi;
             ppj = sh.pj;
-            pend_c = sh.c;
-            pend_s = sh.s;
+            if (pdec == 0) {
+                pend_c = sh.cs[sh.win][0];
+                pend_s = sh.cs[sh.win][1];
+            }
         };
 
         // first selection
