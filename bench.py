@@ -382,6 +382,42 @@ def split_pairs(k):
     return S * (S + 1) // 2
 
 
+def product_config(n, transform):
+    return {"workload": "C = A B, n = %d, A and B N(0,1) FP64 (seeded)" % n, "n": n,
+            "transform": transform, "l2": "L2 flushed (512 MB write) before every step"}
+
+
+def run_product_reference(args, ws, rank):
+    """The oracle's working-precision product (numpy FP64 matmul on the host
+    cores, as in its Sec. 2.1 steps) on the same n: oracle.transform makes
+    two n x n products per call."""
+    if rank != 0:
+        return
+    import oracle
+    n = args.n or 4096
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal((n, n))
+    q = rng.standard_normal((n, n))
+    cores = os.cpu_count()
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.transform(a, q)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            vals.append(2.0 / dt)
+    v = float(np.median(vals))
+    sample = ("oracle.transform (Q^T (A Q), two FP64 n x n products with numpy on %d threads, then the "
+              "symmetrisation) per step at the full n = %d; rate = 2 products / time" % (cores, n))
+    out = {"metric": PRODUCT_METRIC, "value": v, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": product_config(n, args.transform),
+           "cpu_baseline": {"value": v, "unit": "products/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def run_product(args, ws, rank, local):
     import torch
     from paper_2607_23187_b300 import pjac
@@ -431,8 +467,7 @@ def run_product(args, ws, rank, local):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 slices, fp32 accumulate, fp64 result"
            if args.transform == "split_bf16" else "f64", "data": "synthetic",
-           "config": {"workload": "C = A B, n = %d, A and B N(0,1) FP64 (seeded)" % n, "n": n,
-                      "transform": args.transform, "l2": "L2 flushed (512 MB write) before every step"},
+           "config": product_config(n, args.transform),
            "fp64_equivalent_tflops": 2.0 * n ** 3 / (ms / 1000) / 1e12,
            "e2e": None, "gpu_launches": pjac.load().pjac_product_launch_count(h.h, n, n, n) * args.steps,
            "roofline": roof, "clocks": clocks}
@@ -647,6 +682,64 @@ def serving_config(count):
                            "(4 high-priority), CUDA_DEVICE_MAX_CONNECTIONS=32"}
 
 
+def run_serving_reference(args, ws, rank):
+    """The oracle serving the same arrivals one request at a time, first come
+    first served, on the host cores.  Per step, each size's solve time is
+    measured once on the oracle: the preconditioner in full, then at most
+    min(--ref-rotations, 20000) gap-rule rotations, extrapolated to 1.8
+    sweeps of n(n-1)/2 rotations unless the solve converged within them."""
+    if rank != 0:
+        return
+    import oracle
+    import pjac_inputs as pin
+    oracle.build()
+    count = args.requests
+    t_arr, sidx, pool = pin.serving_workload(count=count)
+    sizes = pin.SERVE_SIZES
+    cores = os.cpu_count()
+    budget = min(args.ref_rotations, 20000)
+    vals, p50s, p99s = [], [], []
+    per_size = {}
+    for step in range(args.warmup + args.steps):
+        per_size = {}
+        for k, m in enumerate(sizes):
+            if not np.any(sidx == k):
+                continue
+            p = pool[k][0]
+            t0 = time.perf_counter()
+            q0 = oracle.q0_fp32(p.a)
+            q, a1 = oracle.precondition(p.a, q0)
+            t1 = time.perf_counter()
+            r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=budget)
+            t2 = time.perf_counter()
+            rate = r["rotations"] / max(t2 - t1, 1e-9)
+            need = r["rotations"] if r["status"] == 0 else 1.8 * m * (m - 1) / 2
+            per_size[m] = (t1 - t0) + need / rate
+        fin = 0.0
+        lat = []
+        for q_ in range(count):
+            start = max(t_arr[q_], fin)
+            fin = start + per_size[sizes[sidx[q_]]]
+            lat.append(fin - t_arr[q_])
+        if step >= args.warmup:
+            vals.append(count / (fin - t_arr[0]))
+            p50s.append(float(np.percentile(lat, 50)) * 1000.0)
+            p99s.append(float(np.percentile(lat, 99)) * 1000.0)
+    v = float(np.median(vals))
+    sample = ("one oracle solve per size per step (preconditioner with numpy/LAPACK on %d threads in full, then at "
+              "most %d gap-rule rotations of the C oracle on one thread, extrapolated to 1.8 sweeps), then a "
+              "first-come-first-served queue of the %d arrivals served one at a time" % (cores, budget, count))
+    out = {"metric": SERVING_METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * count / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": serving_config(count),
+           "latency_ms": {"p50": float(np.median(p50s)), "p99": float(np.median(p99s))},
+           "solve_s_per_size": {str(m): t for m, t in per_size.items()},
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def run_serving(args, ws, rank, local):
     import torch
     import pjac_inputs as pin
@@ -772,14 +865,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests of the stream to replay")
     args = ap.parse_args()
-    if args.workload == "serving":
+    if args.workload == "serving" and args.impl == "ours":
         # one hardware queue per serving lane (read when the CUDA context is created)
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     ws, rank, local = dist_init()
     if args.workload == "product":
-        run_product(args, ws, rank, local)
+        if args.impl == "reference":
+            run_product_reference(args, ws, rank)
+        else:
+            run_product(args, ws, rank, local)
     elif args.workload == "serving":
-        run_serving(args, ws, rank, local)
+        if args.impl == "reference":
+            run_serving_reference(args, ws, rank)
+        else:
+            run_serving(args, ws, rank, local)
     elif args.workload == "batched":
         if args.impl == "reference":
             run_batched_reference(args, ws, rank)
