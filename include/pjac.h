@@ -54,7 +54,14 @@ typedef enum {
 typedef enum {
     PJAC_PIVOT_GAP = 0,     /* argmax L_ij of Eq. (1.1) */
     PJAC_PIVOT_GREEDY = 1,  /* argmax |a_ij| (Jacobi 1846) */
-    PJAC_PIVOT_CYCLIC = 2   /* row-cyclic sweeps (0,1),(0,2),...,(n-2,n-1) */
+    PJAC_PIVOT_CYCLIC = 2,  /* row-cyclic sweeps (0,1),(0,2),...,(n-2,n-1) */
+    /* Randomized comparator (Sec. 4.2): every pair equally likely.  Step k
+     * takes z = SplitMix64 output function of (seed + (k+1)*0x9e3779b97f4a7c15)
+     * (Steele, Lea and Flood's generator, used counter-based), i = (z mod 2^32)
+     * mod n, j' = (z div 2^32) mod (n-1), j = j' + [j' >= i], ordered.  A draw
+     * with a_ij == 0 applies the identity and still counts as a rotation.
+     * Off-diagonal stop only. */
+    PJAC_PIVOT_RANDOM = 3
 } pjac_pivot;
 
 /* Stopping rules. */
@@ -83,6 +90,24 @@ typedef struct {
     int ns_steps;            /* Newton--Schulz steps, 0: 3 */
     int cluster_size;        /* CTAs cooperating on one single problem; 0: automatic */
     double time_budget_s;    /* device-side time budget per solve, 0: 600 s */
+    /* 1: no preconditioner -- Algorithm 1 runs directly on A with V0 = I, as
+     * in the paper's Sec. 4.2 experiment (a global orthogonal preconditioner
+     * would spoil the relative accuracy sought there).  0 (default): the
+     * Sec. 2.1 preconditioner runs first.  Applies to pjac_solve,
+     * pjac_solve_batched and the serving calls. */
+    int no_precondition;
+    uint64_t seed;           /* PJAC_PIVOT_RANDOM's seed, default 0 */
+    /* EXTENSION beyond the paper, default 0: first-order refinement steps
+     * applied to (A1, Q) after the Sec. 2.1 preconditioner, each a
+     * simplified step of Ogita and Aishima's iterative refinement for the
+     * symmetric eigenproblem: with A1 = diag(d) + E, D_ij = e_ij/(d_j - d_i)
+     * for pairs with |e_ij| <= 0.01 |d_j - d_i| (the rest are left to
+     * Jacobi), D scaled so its largest absolute row sum is <= 1/4, Z = I + D
+     * made orthogonal by 5 Newton--Schulz steps, then A1 <- Z^T A1 Z,
+     * Q <- Q Z.  Nine working-precision products per step; it resolves the
+     * well-separated pairs on the tensor cores and leaves fewer rotations
+     * to the Jacobi iteration.  0..8. */
+    int refine_steps;
 } pjac_opts;
 
 /* Per-solve report. */
@@ -124,6 +149,23 @@ int pjac_set_opts(pjac_handle* h, const pjac_opts* o);
  */
 int pjac_precondition(pjac_handle* h, const double* A, int n, int lda, const float* Q0,
                       double* Q, int ldq, double* A1, int lda1, void* stream);
+
+/*
+ * The low-precision spectral decomposition of Sec. 2.1 on its own (the first
+ * step of the preconditioner, u_l = single precision as in Sec. 4): the FP32
+ * eigenvector estimate Q0 of fl32(A) that pjac_precondition computes when it
+ * is given no Q0.  Computed on the device by a parallel-order FP32 Jacobi
+ * pass on fl32(A), a Newton--Schulz step pair in working precision and a
+ * refinement pass of the same FP32 Jacobi on X^T fl32(A) X; the result is
+ * rounded to FP32.  Any Q0 with ||Q0^T Q0 - I|| = O(n u_32) and
+ * off(Q0^T fl32(A) Q0) = O(n u_32 ||A||) serves the preconditioner.
+ *   A   [in]  n x n symmetric, lda >= n.  Not modified.
+ *   Q0  [out] n x n FP32, column-major, ldq0 >= n (column k: eigenvector
+ *             estimate; the columns are in no particular order).
+ * Synchronises the stream.  Errors: PJAC_EINVAL (bad sizes, NaN/Inf or
+ * asymmetric input), PJAC_ENOMEM, PJAC_ETIMEOUT, PJAC_ECUDA.
+ */
+int pjac_eig_lowprec(pjac_handle* h, const double* A, int n, int lda, float* Q0, int ldq0, void* stream);
 
 /*
  * Working-precision product C = alpha op(A) op(B) + beta C, computed the way
@@ -184,17 +226,20 @@ int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int lda1, const
  * memory, so a cudaMalloc during a solve would fail or fragment it), or a
  * plug-in that runs inside a host application without access to that
  * application's allocator.  It needs no handle and allocates nothing: its
- * scratch lives in a fixed array of PJAC_NOALLOC_SCRATCH_BYTES that the
- * library places in every GPU's memory when it is loaded, and keeps there
- * until the process exits.
+ * scratch lives in a fixed array of PJAC_NOALLOC_SCRATCH_BYTES in every
+ * GPU's memory, kept there until the process exits.
  *   Arguments, layouts and results are those of pjac_solve_preconditioned
  *   with the default options (off-diagonal stop at tol).
  *   n must not exceed PJAC_NOALLOC_MAX_N; larger n returns PJAC_EINVAL.
- *   The first call on a device looks up the array's device address; make
- *   that first call before any stream capture on that device.
+ *   First call on a device: it looks up the array's device address and
+ *   loads the kernels it launches.  Under CUDA's lazy module loading these
+ *   are the moments the array and the kernels' code take device memory, so
+ *   make the first call on each device (any small valid input will do)
+ *   BEFORE reserving that device's memory; later calls take none.
  *   All calls share the one array: calls whose work overlaps on the GPU
  *   (other streams, other host threads) race on it and must be serialised
- *   by the caller.  The call synchronises the stream.
+ *   by the caller.  The call synchronises the stream and copies its solve
+ *   record to the host, so it cannot be recorded into a CUDA graph.
  */
 #define PJAC_NOALLOC_MAX_N 512
 #define PJAC_NOALLOC_SCRATCH_BYTES ((size_t)PJAC_NOALLOC_MAX_N * PJAC_NOALLOC_MAX_N * 8 + 8192)

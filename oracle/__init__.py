@@ -34,7 +34,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2}
+PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3}
 STOPS = {"offdiag": 0, "libound": 1}
 
 
@@ -86,7 +86,12 @@ def lib():
                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
-                                    ctypes.POINTER(_Info)]
+                                    ctypes.c_uint64, ctypes.POINTER(_Info)]
+            L.or_splitmix64.restype = ctypes.c_uint64
+            L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.or_random_pair.restype = None
+            L.or_random_pair.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
             L.or_jacobi_many.restype = ctypes.c_int
             L.or_jacobi_many.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -149,7 +154,7 @@ def jacobi(a1: np.ndarray, v0: Optional[np.ndarray] = None, pivot: str = "gap",
            stop: str = "offdiag", tol: float = 1e-15, max_rot: Optional[int] = None,
            check_every: Optional[int] = None, select: str = "cache",
            lam: Optional[np.ndarray] = None, eig_tol: float = 0.0,
-           log_len: int = 0, hist_cap: int = 0) -> Dict:
+           log_len: int = 0, hist_cap: int = 0, seed: int = 0) -> Dict:
     """Run Algorithm 1 on a copy of ``a1`` (symmetric FP64), accumulating
     V <- V0 G (identity when v0 is None).
 
@@ -176,7 +181,7 @@ def jacobi(a1: np.ndarray, v0: Optional[np.ndarray] = None, pivot: str = "gap",
     lib().or_jacobi(_ptr(a), n, _ptr(v), PIVOTS[pivot], STOPS[stop], float(tol), int(max_rot),
                     int(check_every), 1 if select == "cache" else 0, _ptr(lam_s), float(eig_tol),
                     _ptr(piv), _ptr(sc), int(log_len), _ptr(hr), _ptr(he), _ptr(ho), int(hist_cap),
-                    ctypes.byref(hl), ctypes.byref(info))
+                    ctypes.byref(hl), ctypes.c_uint64(seed), ctypes.byref(info))
     nl = min(log_len, info.rotations)
     return {
         "a": a, "v": v, "rotations": int(info.rotations), "sweeps": int(info.sweeps),
@@ -188,6 +193,20 @@ def jacobi(a1: np.ndarray, v0: Optional[np.ndarray] = None, pivot: str = "gap",
         "hist_rot": hr[:hl.value].copy(), "hist_err": he[:hl.value].copy(),
         "hist_off": ho[:hl.value].copy(),
     }
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Step k's 64-bit draw of the randomized pivot rule (SplitMix64's
+    output function on the counter seed + (k+1) * 0x9e3779b97f4a7c15)."""
+    return int(lib().or_splitmix64(ctypes.c_uint64(seed), ctypes.c_uint64(k)))
+
+
+def random_pair(seed: int, k: int, n: int) -> Tuple[int, int]:
+    """The pivot (i, j), i < j, of step k of the randomized rule (Sec. 4.2's
+    comparator: every pair equally likely)."""
+    i, j = ctypes.c_int(), ctypes.c_int()
+    lib().or_random_pair(ctypes.c_uint64(seed), int(k), int(n), ctypes.byref(i), ctypes.byref(j))
+    return i.value, j.value
 
 
 def readout(a: np.ndarray, v: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
@@ -282,21 +301,59 @@ def transform_exact(a: np.ndarray, q: np.ndarray) -> np.ndarray:
     return 0.5 * (a1 + a1.T)
 
 
+REFINE_TAU = 0.01          # pairs with |a_ij| > tau |a_jj - a_ii| are left to Jacobi
+REFINE_MAX_ROWSUM = 0.25   # max_i sum_j |D_ij| (>= ||D||_2) is scaled down to at most this
+REFINE_NS_STEPS = 5
+
+
+def refine_step(a1: np.ndarray, q: np.ndarray, tau: float = REFINE_TAU) -> Tuple[np.ndarray, np.ndarray]:
+    """One first-order refinement of the preconditioned pair (A1, Q), an
+    EXTENSION beyond the paper (a simplified step of Ogita and Aishima's
+    iterative refinement for the symmetric eigenvalue problem, 2018): for
+    A1 = diag(d) + E nearly diagonal, the first-order eigenvector correction
+    is I + D with D_ij = e_ij / (d_j - d_i) (antisymmetric, D_ii = 0); pairs
+    with |e_ij| > tau |d_j - d_i| (near-degenerate) get D_ij = 0 and are left
+    to the Jacobi iteration.  D is scaled so that its largest absolute row
+    sum (an upper bound of ||D||_2 for antisymmetric D) is at most 1/4, Z is
+    I + D made orthogonal by Newton--Schulz (5 steps from
+    ||Z^T Z - I||_2 = ||D||_2^2 <= 1/16, which leaves an error near 1e-21),
+    and the pair becomes (Z^T A1 Z symmetrised, Q Z) -- an exact orthogonal
+    similarity up to rounding, so the spectrum is unchanged."""
+    a1 = np.asarray(a1, dtype=np.float64)
+    d = np.diag(a1)
+    delta = d[None, :] - d[:, None]            # d_j - d_i at (i, j)
+    e = a1 - np.diag(d)
+    keep = np.abs(e) <= tau * np.abs(delta)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dm = np.where(keep, e / np.where(keep, delta, 1.0), 0.0)
+    np.fill_diagonal(dm, 0.0)
+    nrm = np.max(np.sum(np.abs(dm), axis=1))
+    if nrm > REFINE_MAX_ROWSUM:
+        dm = dm * (REFINE_MAX_ROWSUM / nrm)
+    z = reorth_ns(np.eye(a1.shape[0]) + dm, REFINE_NS_STEPS)
+    a2 = z.T @ (a1 @ z)
+    return 0.5 * (a2 + a2.T), np.asarray(q, dtype=np.float64) @ z
+
+
 def precondition(a: np.ndarray, q0: Optional[np.ndarray] = None, reorth: str = "ns",
-                 ns_steps: int = 3) -> Tuple[np.ndarray, np.ndarray]:
+                 ns_steps: int = 3, refine_steps: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Sec. 2.1: returns (Q, A1) with Q the FP64-orthogonal preconditioner
-    and A1 = Q^T A Q."""
+    and A1 = Q^T A Q; refine_steps > 0 adds that many ``refine_step``
+    (an extension beyond the paper)."""
     if q0 is None:
         q0 = q0_fp32(a)
     q = reorth_qr(q0) if reorth == "qr" else reorth_ns(q0, ns_steps)
-    return q, transform(a, q)
+    a1 = transform(a, q)
+    for _ in range(refine_steps):
+        a1, q = refine_step(a1, q)
+    return q, a1
 
 
 def solve(a: np.ndarray, pivot: str = "gap", tol: float = 1e-15, q0: Optional[np.ndarray] = None,
-          reorth: str = "ns", ns_steps: int = 3, **kw) -> Dict:
+          reorth: str = "ns", ns_steps: int = 3, refine_steps: int = 0, **kw) -> Dict:
     """Preconditioned Jacobi: Sec. 2.1 preconditioner, then Algorithm 1 on
     A1 with V0 = Q, then the readout."""
-    q, a1 = precondition(a, q0, reorth, ns_steps)
+    q, a1 = precondition(a, q0, reorth, ns_steps, refine_steps)
     r = jacobi(a1, q, pivot=pivot, tol=tol, **kw)
     w, v = readout(r["a"], r["v"])
     r.update({"w": w, "v_sorted": v, "q": q, "a1": a1})

@@ -46,7 +46,17 @@
  *     squaring (Eq. (1.1) is homogeneous of degree one, t and c of degree 0).
  *   - Convergence (Alg. 1 "Not convergent"): off(A) = sqrt(sum_{k!=l} a_kl^2)
  *     <= tol*||A||_F, tested before every `check_every`-th rotation (greedy,
- *     gap) or before every sweep (cyclic).
+ *     gap, random) or before every sweep (cyclic).
+ *   - Randomized pivoting (the comparator of Sec. 4.2: every pair (i,j)
+ *     drawn with equal probability): step k draws the 64-bit word
+ *     z = SplitMix64(seed + (k+1)*0x9e3779b97f4a7c15) -- the mixing function
+ *     of Steele, Lea and Flood's SplitMix64 generator, used counter-based so
+ *     that any step's draw is known without the ones before it -- and takes
+ *     i = (z mod 2^32) mod n, j' = (z div 2^32) mod (n-1), j = j' + [j' >= i],
+ *     then orders the pair.  Every ordered pair, hence every unordered pair,
+ *     has the same probability up to a bias below n/2^32.  A draw whose
+ *     a_ij is exactly zero applies the identity rotation and still counts
+ *     as a step.
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,6 +66,7 @@
 #define OR_PIVOT_GAP 0
 #define OR_PIVOT_GREEDY 1
 #define OR_PIVOT_CYCLIC 2
+#define OR_PIVOT_RANDOM 3
 #define OR_STOP_OFFDIAG 0
 #define OR_STOP_LIBOUND 1
 
@@ -112,6 +123,24 @@ void or_rotation(double aii, double ajj, double aij, double* c, double* s, doubl
     *t = tt;
     *c = cc;
     *s = tt * cc;
+}
+
+/* SplitMix64's output function applied to the counter seed + (k+1) gamma. */
+uint64_t or_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* The pair of step k of the randomized rule (see the header). */
+void or_random_pair(uint64_t seed, long long k, int n, int* pi, int* pj) {
+    uint64_t z = or_splitmix64(seed, (uint64_t)k);
+    int i = (int)((uint32_t)z % (uint32_t)n);
+    int j = (int)((uint32_t)(z >> 32) % (uint32_t)(n - 1));
+    if (j >= i) j++;
+    *pi = i < j ? i : j;
+    *pj = i < j ? j : i;
 }
 
 static double or_score(int pivot, const double* A, int n, int k, int l) {
@@ -299,7 +328,7 @@ int or_jacobi(double* A, int n, double* V, int pivot, int stop, double tol,
               const double* lam_sorted, double eig_tol,
               int* piv_log, double* score_log, long long log_len,
               long long* hist_rot, double* hist_err, double* hist_off, long long hist_cap,
-              long long* hist_len, or_info* info) {
+              long long* hist_len, uint64_t seed, or_info* info) {
     memset(info, 0, sizeof(*info));
     info->first_rot_eig_ok = -1;
     if (hist_len) *hist_len = 0;
@@ -356,6 +385,21 @@ int or_jacobi(double* A, int n, double* V, int pivot, int stop, double tol,
         }
     }
 
+    if (pivot == OR_PIVOT_RANDOM) {
+        for (;;) {
+            if (rot % check_every == 0) OR_CHECK_AND_MAYBE_STOP();
+            if (rot >= max_rot) { status = 1; goto done; }
+            int i, j;
+            or_random_pair(seed, rot, n, &i, &j);
+            if (piv_log && rot < log_len) {
+                piv_log[2 * rot] = i; piv_log[2 * rot + 1] = j;
+                if (score_log) score_log[rot] = fabs(A[(size_t)i * n + j]);
+            }
+            or_rotate(A, n, V, i, j, NULL);
+            rot++;
+        }
+    }
+
     if (select_mode == 1) {
         bestv = (double*)malloc(sizeof(double) * (size_t)n);
         bestc = (int*)malloc(sizeof(int) * (size_t)n);
@@ -404,7 +448,7 @@ int or_jacobi_many(int count, const int* ns, const long long* a_off, double* A,
         int n = ns[p];
         long long mr = max_rot_per_n2 * (long long)n * (long long)n;
         or_jacobi(A + a_off[p], n, V ? V + v_off[p] : NULL, pivot, stop, tol, mr, n, 1,
-                  NULL, 0.0, NULL, NULL, 0, NULL, NULL, NULL, 0, NULL, &inf);
+                  NULL, 0.0, NULL, NULL, 0, NULL, NULL, NULL, 0, NULL, 0, &inf);
         rotations[p] = inf.rotations;
         status[p] = inf.status;
     }

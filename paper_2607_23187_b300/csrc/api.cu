@@ -79,6 +79,9 @@ extern "C" void pjac_default_opts(pjac_opts* o) {
     o->ns_steps = 3;
     o->cluster_size = 0;
     o->time_budget_s = 600.0;
+    o->no_precondition = 0;
+    o->seed = 0;
+    o->refine_steps = 0;
 }
 
 static int validate_opts(const pjac_opts* o) {
@@ -91,6 +94,9 @@ static int validate_opts(const pjac_opts* o) {
     if (o->ns_steps < 0 || o->ns_steps > 10) return set_err(PJAC_EINVAL, "opts.ns_steps must be in [0,10]");
     if (o->cluster_size < 0 || o->cluster_size > 16 || (o->cluster_size & (o->cluster_size - 1)))
         return set_err(PJAC_EINVAL, "opts.cluster_size must be 0 or a power of two <= 16");
+    if (o->no_precondition != 0 && o->no_precondition != 1)
+        return set_err(PJAC_EINVAL, "opts.no_precondition must be 0 or 1");
+    if (o->refine_steps < 0 || o->refine_steps > 8) return set_err(PJAC_EINVAL, "opts.refine_steps must be in [0,8]");
     return PJAC_OK;
 }
 
@@ -176,21 +182,24 @@ struct SolveWs {
     int* rank;     // n
     int* flag;     // 1
     DevInfo* info; // 1
+    double* Z;     // n x n (refinement)
+    unsigned long long* maxsum;   // 1 (refinement)
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     size_t nn = (size_t)n * n;
-    size_t sz[10] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
-                     diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo)};
+    const size_t nz = h->opts.refine_steps > 0 ? nn * 8 : 8;
+    size_t sz[12] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
+                     diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo), nz, 8};
     size_t tot = 0;
     for (size_t s : sz) tot += align256(s);
     int r = h->ws.ensure(tot, st);
     if (r) return r;
     char* p = static_cast<char*>(h->ws.p);
-    void* ptrs[10];
-    for (int k = 0; k < 10; ++k) {
+    void* ptrs[12];
+    for (int k = 0; k < 12; ++k) {
         ptrs[k] = p;
         p += align256(sz[k]);
     }
@@ -204,6 +213,8 @@ static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     w->rank = (int*)ptrs[7];
     w->flag = (int*)ptrs[8];
     w->info = (DevInfo*)ptrs[9];
+    w->Z = (double*)ptrs[10];
+    w->maxsum = (unsigned long long*)ptrs[11];
     return PJAC_OK;
 }
 
@@ -269,6 +280,52 @@ static int newton_schulz(pjac_handle* h, double* Q, long long ldq, int n, int st
     return PJAC_OK;
 }
 
+// The low-precision spectral decomposition of Sec. 2.1 (u_l = single, as in
+// Sec. 4) into Q (FP64 storage, ld ldq): an FP32 eigenbasis X of fl32(A).
+// The parallel-order FP32 Jacobi pass leaves its basis off by the rounding of
+// its many rotation layers, in the eigenvectors and in orthogonality (each
+// FP32 rotation moves column norms by a rounding unit).  So: X = fl64(Q0)
+// made orthogonal (Newton--Schulz), then a refinement pass on
+// B = X^T fl32(A) X that diagonalises it further, X <- X (I + D).
+static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, double* Q, long long ldq,
+                         SolveWs& w, cudaStream_t st) {
+    CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, h->coop_cap, st));
+    CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
+    int r = newton_schulz(h, Q, ldq, n, 2, w, st);
+    if (r) return r;
+    CK(round_to_fp32(A, lda, w.Y, n, n, st));                             // Y = fl32(A)
+    r = product(h, false, false, n, 1.0, w.Y, n, Q, ldq, 0.0, w.T, n, st);    // T = fl32(A) X
+    if (r) return r;
+    r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
+    if (r) return r;
+    CK(symmetrize(w.Y, n, n, st));
+    CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, h->coop_cap, st));                        // D
+    CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
+    r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);    // X D
+    if (r) return r;
+    CK(add_f64(Q, ldq, w.Y, n, n, st));                                   // X (I + D)
+    return PJAC_OK;
+}
+
+// One first-order refinement step of (A1, Q) (pjac_opts.refine_steps, an
+// extension beyond the paper): Z = I + s D from A1, made orthogonal by
+// Newton--Schulz, then A1 <- Z^T A1 Z (symmetrised) and Q <- Q Z.
+static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, long long ldq, int n, SolveWs& w,
+                       cudaStream_t st) {
+    CK(refine_build(A1, lda1, n, REFINE_TAU, w.Z, w.maxsum, REFINE_MAX_ROWSUM, st));
+    int r = newton_schulz(h, w.Z, n, n, REFINE_NS_STEPS, w, st);
+    if (r) return r;
+    r = product(h, false, false, n, 1.0, A1, lda1, w.Z, n, 0.0, w.T, n, st);   // T = A1 Z
+    if (r) return r;
+    r = product(h, true, false, n, 1.0, w.Z, n, w.T, n, 0.0, A1, lda1, st);   // A1 = Z^T T
+    if (r) return r;
+    CK(symmetrize(A1, lda1, n, st));
+    r = product(h, false, false, n, 1.0, Q, ldq, w.Z, n, 0.0, w.T, n, st);     // T = Q Z
+    if (r) return r;
+    CK(copy_f64(w.T, n, Q, ldq, n, n, st));
+    return PJAC_OK;
+}
+
 // Sec. 2.1 into workspace: Q (ld n) and A1 (ld n).  Records ev[0..2].
 static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda, const float* Q0,
                            double* Q, long long ldq, double* A1, long long lda1, SolveWs& w, cudaStream_t st) {
@@ -279,29 +336,10 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         // X = fl64(Q0) as given
         CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
     } else {
-        // FP32 spectral decomposition of fl32(A) (Sec. 2.1 with u_l = single,
-        // as in Sec. 4).  The parallel-order FP32 Jacobi pass leaves its
-        // basis off by the rounding of its many rotation layers, in the
-        // eigenvectors and in orthogonality (each FP32 rotation moves column
-        // norms by a rounding unit).  So: X = fl64(Q0) made orthogonal
-        // (Newton--Schulz), then a refinement pass on B = X^T fl32(A) X
-        // that diagonalises it further, X <- X (I + D).  After the final
-        // reorthogonalisation below, fl32(A) = Q Lambda Q^T to FP32 accuracy.
-        CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, h->coop_cap, st));
-        CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
-        int r = newton_schulz(h, Q, ldq, n, 2, w, st);
+        // after the final reorthogonalisation below, fl32(A) = Q Lambda Q^T
+        // to FP32 accuracy
+        int r = lowprec_basis(h, A, n, lda, Q, ldq, w, st);
         if (r) return r;
-        CK(round_to_fp32(A, lda, w.Y, n, n, st));                             // Y = fl32(A)
-        r = product(h, false, false, n, 1.0, w.Y, n, Q, ldq, 0.0, w.T, n, st);    // T = fl32(A) X
-        if (r) return r;
-        r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
-        if (r) return r;
-        CK(symmetrize(w.Y, n, n, st));
-        CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, h->coop_cap, st));                        // D
-        CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
-        r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);    // X D
-        if (r) return r;
-        CK(add_f64(Q, ldq, w.Y, n, n, st));                                   // X (I + D)
     }
     int r = newton_schulz(h, Q, ldq, n, h->opts.ns_steps, w, st);
     if (r) return r;
@@ -312,6 +350,10 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
     r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
     if (r) return r;
     CK(symmetrize(A1, lda1, n, st));
+    for (int k = 0; k < h->opts.refine_steps; ++k) {
+        r = refine_step(h, A1, lda1, Q, ldq, n, w, st);
+        if (r) return r;
+    }
     CK(cudaEventRecord(h->ev[2], st));
     return PJAC_OK;
 }
@@ -335,6 +377,30 @@ extern "C" int pjac_precondition(pjac_handle* h, const double* A, int n, int lda
     return tc_status(h, st);
 }
 
+extern "C" int pjac_eig_lowprec(pjac_handle* h, const double* A, int n, int lda, float* Q0, int ldq0,
+                                void* stream) {
+    if (!h || !A || !Q0) return set_err(PJAC_EINVAL, "NULL argument");
+    int r = check_dims(n, lda, "lda");
+    if (!r) r = check_dims(n, ldq0, "ldq0");
+    if (r) return r;
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveWs w;
+    r = layout_ws(h, n, &w, st);
+    if (r) return r;
+    r = check_input(h, A, lda, n, st, w.flag);
+    if (r) return r;
+    r = tc_prepare(h, n, n, n, st);
+    if (r) return r;
+    r = lowprec_basis(h, A, n, lda, w.Vw, n, w, st);
+    if (r) return r;
+    CK(copy_f64_to_f32(w.Vw, n, Q0, ldq0, n, st));
+    r = tc_status(h, st);
+    if (r) return r;
+    CK(cudaStreamSynchronize(st));
+    return PJAC_OK;
+}
+
 extern "C" int pjac_product(pjac_handle* h, int transa, int transb, int m, int n, int k, double alpha,
                             const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
                             void* stream) {
@@ -354,9 +420,11 @@ extern "C" int pjac_product(pjac_handle* h, int transa, int transb, int m, int n
     return tc_status(h, st);
 }
 
-static long long budget_cycles(const pjac_opts& o) {
+// The device checks its time budget against the GPU's global nanosecond
+// timer (%globaltimer), so the budget is wall time whatever the SM clock.
+static long long budget_ns(const pjac_opts& o) {
     double s = o.time_budget_s > 0 ? o.time_budget_s : 600.0;
-    return (long long)(s * 2.2e9);   // cycles at the maximum SM clock (upper bound on time)
+    return (long long)(s * 1e9);
 }
 
 static int run_jacobi(pjac_handle* h, double* A1, long long lda1, int n, double* Vw, long long ldvw,
@@ -374,8 +442,9 @@ static int run_jacobi(pjac_handle* h, double* A1, long long lda1, int n, double*
     long long pairs = (long long)n * (n - 1) / 2;
     a.max_rot = h->opts.max_rotations > 0 ? h->opts.max_rotations : 50 * pairs;
     a.check_every = h->opts.check_every > 0 ? h->opts.check_every : n;
-    a.budget_cycles = budget_cycles(h->opts);
+    a.budget_ns = budget_ns(h->opts);
     a.info = dinfo;
+    a.seed = h->opts.seed;
     int P = h->opts.cluster_size > 0 ? h->opts.cluster_size : jacobi_auto_cluster(n);
     while (P > 1 && (n + P - 1) / P < 8) P >>= 1;
     if ((n + P - 1) / P > 1024) return set_err(PJAC_EINVAL, "n = %d needs a larger cluster", n);
@@ -427,7 +496,7 @@ static int solve_checks(pjac_handle* h, const double* A, int n, int lda, pjac_pi
     int r = check_dims(n, lda, "lda");
     if (!r && V) r = check_dims(n, ldv, "ldv");
     if (r) return r;
-    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     if (h->opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
         return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
@@ -435,14 +504,25 @@ static int solve_checks(pjac_handle* h, const double* A, int n, int lda, pjac_pi
 }
 
 // Preconditioner, Jacobi, readout: all enqueued on st, no host round trip.
+// Without the preconditioner (opts.no_precondition) Algorithm 1 starts from
+// A1 = A and V0 = I.
 static int solve_pipeline(pjac_handle* h, const double* A, int n, int lda, pjac_pivot pivot, double tol,
                           double* W, double* V, int ldv, SolveWs& w, cudaStream_t st) {
-    int r = precondition_ws(h, A, n, lda, nullptr, w.Vw, n, w.A1, n, w, st);
-    if (r) return r;
+    int r;
+    if (h->opts.no_precondition) {
+        CK(cudaEventRecord(h->ev[0], st));
+        CK(cudaEventRecord(h->ev[1], st));
+        CK(copy_f64(A, lda, w.A1, n, n, n, st));
+        CK(set_identity(w.Vw, n, n, st));
+        CK(cudaEventRecord(h->ev[2], st));
+    } else {
+        r = precondition_ws(h, A, n, lda, nullptr, w.Vw, n, w.A1, n, w, st);
+        if (r) return r;
+    }
     r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
     if (r) return r;
     CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
-    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16)
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16 && !h->opts.no_precondition)
         CK(gemm_split_bf16_fold_status(h->tcws.p, w.info, st));   // a timed-out product fails the solve
     CK(cudaEventRecord(h->ev[3], st));
     return PJAC_OK;
@@ -492,7 +572,7 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
     if (!r && V0) r = check_dims(n, ldv0, "ldv0");
     if (!r && V) r = check_dims(n, ldv, "ldv");
     if (r) return r;
-    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     if (h->opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
         return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
@@ -522,6 +602,9 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
 extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     if (!h || n < 1 || n > PJAC_MAX_N) return -1;
     if (n == 1) return 0;
+    // without the preconditioner: input check, copy of A, V0 = I, Jacobi,
+    // readout (two kernels)
+    if (h->opts.no_precondition) return 6;
     const bool split = h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16;
     const int P = split ? gemm_split_bf16_launches(n, n, n) : 1;   // launches per product
     const int ns = h->opts.ns_steps;
@@ -534,6 +617,9 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
     // transform (two products) and symmetrise, Jacobi, readout (two kernels)
     c += 2 * P + 1 + 1 + 2;
+    // refinement steps: build and scale, Newton--Schulz, three products,
+    // symmetrise, copy
+    c += h->opts.refine_steps * (2 + REFINE_NS_STEPS * (2 * P + 2) + 3 * P + 2);
     if (split) c += 1;  // product status folded into the solve record
     return c;
 }

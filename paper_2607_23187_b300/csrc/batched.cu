@@ -262,6 +262,101 @@ __global__ void __launch_bounds__(BT) b_precond_kernel(const BatchDesc* desc, in
     }
 }
 
+// Stage 2b: first-order refinement steps of (A1, V) (see pjac_opts.
+// refine_steps): Z = I + s D with D_ij = a_ij/(a_jj - a_ii) for the pairs
+// with |a_ij| <= tau |a_jj - a_ii| (else 0), s scaling the largest absolute
+// row sum of D to at most 1/4; Z made orthogonal by Newton--Schulz (steps
+// until the bound on ||Z^T Z - I|| falls below 1e-20, at most 5); then
+// A1 <- Z^T A1 Z symmetrised, V <- V Z.  The parallel FP32 pass of stage 1
+// leaves its basis off orthogonality by the rounding of its rotation layers,
+// which Newton--Schulz turns into off-diagonal entries of A1 near that
+// level; one step brings them back to FP32 accuracy.
+__global__ void __launch_bounds__(BT) b_refine_kernel(const BatchDesc* desc, int nb, const int* order,
+                                                      int* counter, int steps) {
+    __shared__ double Xs[16][65], Ys[16][65];
+    __shared__ double red[BT / 32];
+    __shared__ int next;
+    for (;;) {
+        int t = take_problem(counter, &next);
+        if (t >= nb) break;
+        BatchDesc d = desc[order[t]];
+        const int n = d.n;
+        for (int step = 0; step < steps; ++step) {
+            // D, and its largest absolute row (= column) sum
+            double mx = 0.0;
+            for (int j = threadIdx.x; j < n; j += BT) {
+                const double dj = d.A[j + j * n];
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    double v = 0.0;
+                    if (i != j) {
+                        const double e = d.A[i + j * n];
+                        const double dl = __dadd_rn(dj, -d.A[i + i * n]);
+                        if (fabs(e) <= __dmul_rn(REFINE_TAU, fabs(dl)) && dl != 0.0) v = __ddiv_rn(e, dl);
+                    }
+                    d.Z[i + j * n] = v;
+                    acc = __dadd_rn(acc, fabs(v));
+                }
+                mx = fmax(mx, acc);
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+            __syncthreads();
+            double m = 0.0;
+            for (int w = 0; w < BT / 32; ++w) m = fmax(m, red[w]);
+            const double sc = (m > REFINE_MAX_ROWSUM) ? __ddiv_rn(REFINE_MAX_ROWSUM, m) : 1.0;
+            const double rho = fmin(m, REFINE_MAX_ROWSUM);
+            for (int e = threadIdx.x; e < n * n; e += BT) {
+                const int r = e % n, c = e / n;
+                d.Z[e] = (r == c) ? 1.0 : __dmul_rn(sc, d.Z[e]);
+            }
+            __syncthreads();
+            // Newton--Schulz: ||Z^T Z - I|| <= rho^2 = e0, e_{k+1} <= 3/4 e_k^2 + e_k^3/4
+            int ns = 0;
+            for (double eb = rho * rho; eb > 1e-20 && ns < REFINE_NS_STEPS; eb = 0.75 * eb * eb + 0.25 * eb * eb * eb)
+                ++ns;
+            for (int it = 0; it < ns; ++it) {
+                cta_gemm(true, false, n, 1.0, d.Z, d.Z, d.Y, Xs, Ys);
+                for (int e = threadIdx.x; e < n * n; e += BT) {
+                    int r = e % n, c = e / n;
+                    d.Y[e] = ((r == c) ? 3.0 : 0.0) - d.Y[e];
+                }
+                __syncthreads();
+                cta_gemm(false, false, n, 0.5, d.Z, d.Y, d.T, Xs, Ys);
+                for (int e = threadIdx.x; e < n * n; e += BT) d.Z[e] = d.T[e];
+                __syncthreads();
+            }
+            cta_gemm(false, false, n, 1.0, d.A, d.Z, d.T, Xs, Ys);   // T = A1 Z
+            cta_gemm(true, false, n, 1.0, d.Z, d.T, d.A, Xs, Ys);    // A1 = Z^T T
+            for (int e = threadIdx.x; e < n * n; e += BT) {
+                int r = e % n, c = e / n;
+                if (r < c) {
+                    double v = 0.5 * (d.A[r + c * n] + d.A[c + r * n]);
+                    d.A[r + c * n] = v;
+                    d.A[c + r * n] = v;
+                }
+            }
+            __syncthreads();
+            cta_gemm(false, false, n, 1.0, d.V, d.Z, d.T, Xs, Ys);   // T = V Z
+            for (int e = threadIdx.x; e < n * n; e += BT) d.V[e] = d.T[e];
+            __syncthreads();
+        }
+    }
+}
+
+// Without the preconditioner: A1 = A and V0 = I for every problem.
+__global__ void __launch_bounds__(BT) b_copyin_kernel(const BatchDesc* desc, int nb) {
+    const int p = blockIdx.x;
+    if (p >= nb) return;
+    const BatchDesc d = desc[p];
+    const int n = d.n;
+    for (int e = threadIdx.x; e < n * n; e += BT) {
+        const int r = e % n, c = e / n;
+        d.A[e] = d.Ain[e];
+        d.V[e] = (r == c) ? 1.0 : 0.0;
+    }
+}
+
 // Loads this file's kernels on the current device: asking for a kernel's
 // attributes loads it, where a first launch would otherwise do so later.
 cudaError_t preload_batched_kernels() {
@@ -269,12 +364,15 @@ cudaError_t preload_batched_kernels() {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_diag32_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_precond_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_copyin_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, b_refine_kernel);
     return e;
 }
 
 // Kernel launches of one pjac_solve_batched call: FP32 diagonaliser,
-// preconditioner, Jacobi, readout, report.
-int batched_launch_count() { return 5; }
+// preconditioner, refinement, Jacobi, readout, report (without the
+// preconditioner: the copy-in replaces the first three).
+int batched_launch_count(int no_precondition) { return no_precondition ? 4 : 6; }
 
 }  // namespace pjac
 
@@ -317,7 +415,7 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     if (!h || !n || !a_off || !A || !w_off || !W || !infos) return set_err(PJAC_EINVAL, "NULL argument");
     if (V && !v_off) return set_err(PJAC_EINVAL, "v_off is NULL while V is not");
     if (nb < 1) return set_err(PJAC_EINVAL, "nb = %d < 1", nb);
-    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     pjac_opts opts;
     handle_opts(h, &opts);
@@ -330,7 +428,7 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
         if (a_off[p] < 0 || w_off[p] < 0 || (V && v_off[p] < 0)) return set_err(PJAC_EINVAL, "negative offset");
         max_n = std::max(max_n, n[p]);
         size_t nn = (size_t)n[p] * n[p];
-        ws += a256(nn * 8) * 4 + a256((size_t)n[p] * 8) + a256(nn * 4) * 2 + a256(sizeof(DevInfo));
+        ws += a256(nn * 8) * 5 + a256((size_t)n[p] * 8) + a256(nn * 4) * 2 + a256(sizeof(DevInfo));
     }
     size_t hdr = a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb) + 256;
     size_t need = hdr + ws;
@@ -392,6 +490,7 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
         d.V = reinterpret_cast<double*>(p); p += a256(nn * 8);
         d.T = reinterpret_cast<double*>(p); p += a256(nn * 8);
         d.Y = reinterpret_cast<double*>(p); p += a256(nn * 8);
+        d.Z = reinterpret_cast<double*>(p); p += a256(nn * 8);
         d.Wd = reinterpret_cast<double*>(p); p += a256(m * 8);
         d.A32 = reinterpret_cast<float*>(p); p += a256(nn * 4);
         d.Q32 = reinterpret_cast<float*>(p); p += a256(nn * 4);
@@ -407,21 +506,31 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
 #define BK(call) do { e = (call); if (e != cudaSuccess) return cuda_err(e, #call); } while (0)
     BK(cudaMemcpyAsync(d_desc, h_desc, sizeof(BatchDesc) * nb, cudaMemcpyHostToDevice, st));
     BK(cudaMemcpyAsync(d_order, h_order, sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-    BK(cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), st));
+    BK(cudaMemsetAsync(d_counters, 0, 8 * sizeof(int), st));
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int ctas = std::min(nb, sms * 2);
     size_t smem32 = (size_t)2 * SMEM_N32 * SMEM_N32 * sizeof(float);
     BK(cudaFuncSetAttribute(b_diag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-    b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 40);
-    BK(cudaGetLastError());
-    int ns = opts.ns_steps;
-    b_precond_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 1, ns);
-    BK(cudaGetLastError());
-    long long budget = (long long)((opts.time_budget_s > 0 ? opts.time_budget_s : 600.0) * 2.2e9);
+    if (opts.no_precondition) {
+        b_copyin_kernel<<<nb, BT, 0, st>>>(d_desc, nb);
+        BK(cudaGetLastError());
+    } else {
+        b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 40);
+        BK(cudaGetLastError());
+        int ns = opts.ns_steps;
+        b_precond_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 1, ns);
+        BK(cudaGetLastError());
+        // one refinement step restores the FP32-accurate basis (see
+        // b_refine_kernel); opts.refine_steps adds more
+        b_refine_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 3,
+                                                              1 + opts.refine_steps);
+        BK(cudaGetLastError());
+    }
+    long long budget = (long long)((opts.time_budget_s > 0 ? opts.time_budget_s : 600.0) * 1e9);   // ns
     BK(launch_jacobi_batched(d_desc, nb, d_order, d_counters + 2, (int)pivot, (int)opts.stop, tol, 25, budget,
-                             max_n, std::min(nb, sms * 2), st));
+                             max_n, std::min(nb, sms * 2), opts.seed, st));
     BK(launch_readout_batched(d_desc, nb, max_n, st));
     BK(launch_info_batched(d_desc, nb, infos, st));   // keep batched_launch_count() in step
 #undef BK

@@ -24,6 +24,13 @@
 
 namespace pjac {
 
+// The GPU's global nanosecond timer (wall time, independent of the SM clock).
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ int scale_exp(double d, double q) {
     double m = fmax(fabs(d), fabs(q));
     if (m > 0x1p+500 || m < 0x1p-500) return ilogb(m);
@@ -202,6 +209,22 @@ __device__ __forceinline__ int gap_key(double x, double dd) {
 __device__ __forceinline__ int greedy_key(double x) {
     unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
     return (int)(bx >> 32);
+}
+
+// The randomized pivot rule's pair of step k (Sec. 4.2's comparator: every
+// pair equally likely).  The draw is the output function of Steele, Lea and
+// Flood's SplitMix64 generator applied to the counter seed + (k+1) gamma;
+// its low word picks i among n, its high word j among the other n-1.
+__device__ __forceinline__ void random_pair(unsigned long long seed, long long k, int n, int& i, int& j) {
+    unsigned long long z = seed + (unsigned long long)(k + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    const int a = (int)((unsigned)z % (unsigned)n);
+    int b = (int)((unsigned)(z >> 32) % (unsigned)(n - 1));
+    if (b >= a) b++;
+    i = min(a, b);
+    j = max(a, b);
 }
 
 // Order-preserving 64-bit integer image of a double (for sorting W).

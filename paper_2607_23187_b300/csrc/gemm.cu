@@ -142,6 +142,77 @@ cudaError_t copy_f64(const double* src, long long lds, double* dst, long long ld
     return cudaGetLastError();
 }
 
+__global__ void copy_f64_f32_kernel(const double* s, long long lds, float* d, long long ldd, int n) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nn = (long long)n * n;
+    for (; e < nn; e += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(e % n), c = (int)(e / n);
+        d[(long long)c * ldd + r] = __double2float_rn(s[(long long)c * lds + r]);
+    }
+}
+
+cudaError_t copy_f64_to_f32(const double* src, long long lds, float* dst, long long ldd, int n, cudaStream_t st) {
+    long long nn = (long long)n * n;
+    int blocks = (int)((nn + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    copy_f64_f32_kernel<<<blocks, 256, 0, st>>>(src, lds, dst, ldd, n);
+    return cudaGetLastError();
+}
+
+// First-order refinement (see pjac_opts.refine_steps): Z = D with
+// D_ij = e_ij / (d_j - d_i) where |e_ij| <= tau |d_j - d_i|, else 0, for the
+// nearly diagonal A1 = diag(d) + E.  One CTA per column j; the column's
+// absolute sum (the row sum of the antisymmetric D) goes into a running
+// maximum (non-negative doubles order like their bit patterns).
+__global__ void refine_build_kernel(const double* A1, long long lda1, int n, double tau, double* Z,
+                                    unsigned long long* maxsum) {
+    const int j = blockIdx.x;
+    __shared__ double red[8];
+    const double dj = A1[(long long)j * lda1 + j];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = 0.0;
+        if (i != j) {
+            const double e = A1[(long long)j * lda1 + i];
+            const double dl = __dadd_rn(dj, -A1[(long long)i * lda1 + i]);
+            if (fabs(e) <= __dmul_rn(tau, fabs(dl)) && dl != 0.0) v = __ddiv_rn(e, dl);
+        }
+        Z[(long long)j * n + i] = v;
+        acc = __dadd_rn(acc, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __dadd_rn(t, red[w]);
+        atomicMax(maxsum, (unsigned long long)__double_as_longlong(t));
+    }
+}
+
+// Z <- I + s D with s = min(1, limit / max row sum).
+__global__ void refine_scale_kernel(double* Z, int n, const unsigned long long* maxsum, double limit) {
+    const double m = __longlong_as_double((long long)*maxsum);
+    const double s = (m > limit) ? __ddiv_rn(limit, m) : 1.0;
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        Z[e] = (r == c) ? 1.0 : __dmul_rn(s, Z[e]);
+    }
+}
+
+cudaError_t refine_build(const double* A1, long long lda1, int n, double tau, double* Z,
+                         unsigned long long* maxsum, double limit, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(maxsum, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    refine_build_kernel<<<n, 256, 0, st>>>(A1, lda1, n, tau, Z, maxsum);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    refine_scale_kernel<<<592, 256, 0, st>>>(Z, n, maxsum, limit);
+    return cudaGetLastError();
+}
+
 __global__ void identity_kernel(double* d, long long ldd, int n) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tot = (long long)n * n;
@@ -235,6 +306,9 @@ cudaError_t preload_gemm_kernels() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, add_f64_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, three_i_minus_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, check_finite_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, copy_f64_f32_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_build_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_scale_kernel);
     return e;
 }
 

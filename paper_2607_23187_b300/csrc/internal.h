@@ -30,8 +30,9 @@ struct JacArgs {
     double tol;
     long long max_rot;
     long long check_every;
-    long long budget_cycles;
+    long long budget_ns;
     DevInfo* info;
+    unsigned long long seed;   // PJAC_PIVOT_RANDOM
 };
 
 // One problem of the batched form, as the device sees it.  All matrices
@@ -42,6 +43,7 @@ struct BatchDesc {
     double* V;             // Q, then the accumulated V
     double* T;             // product temporaries
     double* Y;
+    double* Z;             // refinement rotation
     double* Wd;            // unsorted diagonal
     float* A32;            // FP32 diagonaliser state (used when n > 128)
     float* Q32;            // FP32 eigenvector estimate Q0
@@ -57,8 +59,8 @@ cudaError_t launch_jacobi(const JacArgs& a, int cluster, cudaStream_t st);
 int jacobi_auto_cluster(int n);
 cudaError_t launch_jacobi_batched(const BatchDesc* d_desc, int nb, const int* d_order,
                                   int* d_counter, int pivot, int stop, double tol,
-                                  long long max_rot_per_n2, long long budget_cycles, int max_n,
-                                  int ctas, cudaStream_t st);
+                                  long long max_rot_per_n2, long long budget_ns, int max_n,
+                                  int ctas, unsigned long long seed, cudaStream_t st);
 cudaError_t launch_readout(const double* Wd, const double* Vws, long long ldvws, int n,
                            double* W, double* V, long long ldv, int* rank_ws, cudaStream_t st);
 cudaError_t launch_readout_batched(const BatchDesc* d_desc, int nb, int max_n, cudaStream_t st);
@@ -77,6 +79,13 @@ cudaError_t copy_f32_to_f64(const float* src, long long lds, double* dst, long l
 cudaError_t copy_f64(const double* src, long long lds, double* dst, long long ldd, int m, int n,
                      cudaStream_t st);
 cudaError_t set_identity(double* dst, long long ldd, int n, cudaStream_t st);
+cudaError_t copy_f64_to_f32(const double* src, long long lds, float* dst, long long ldd, int n, cudaStream_t st);
+// first-order refinement (pjac_opts.refine_steps): Z = I + s D built from A1
+constexpr double REFINE_TAU = 0.01;
+constexpr double REFINE_MAX_ROWSUM = 0.25;
+constexpr int REFINE_NS_STEPS = 5;
+cudaError_t refine_build(const double* A1, long long lda1, int n, double tau, double* Z,
+                         unsigned long long* maxsum, double limit, cudaStream_t st);
 cudaError_t three_i_minus(double* Y, long long ldy, int n, cudaStream_t st);
 cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cudaStream_t st);
 
@@ -109,6 +118,6 @@ cudaError_t preload_gemm_kernels();
 cudaError_t preload_tc_kernels();
 cudaError_t preload_jacobi_kernels();
 
-int batched_launch_count();
+int batched_launch_count(int no_precondition);
 
 }  // namespace pjac

@@ -545,7 +545,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     const int k0 = min(n, rank * mchunk);
     const int k1 = min(n, k0 + mchunk);
     const int pivot = a.pivot;
-    long long start = clock64();
+    const unsigned long long start = now_ns();
 #ifdef PJAC_PROFILE
     long long pt = clock64();
     unsigned int pex = 0;
@@ -614,7 +614,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         double part = owned_offsum(a, k0, k1, sh.scale, sh);
         if (tid == 0) {
             sh.slots[par].sum = part;
-            sh.slots[par].flags = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
+            sh.slots[par].flags = (rank == 0 && a.budget_ns > 0 && (long long)(now_ns() - start) > a.budget_ns) ? 1 : 0;
         }
         cta_exchange_sync<CLUSTER>();
         if (tid == 0) {
@@ -658,7 +658,8 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     // pI (pJ): this thread's best entry of the new row i (row j) over its
     // owned columns; kI (kJ): the two largest keys among them.
     auto rotate_owned = [&](int i, int j, const double c, const double s, const double dii_new,
-                            const double djj_new, bool score, Cand& pI, Cand& pJ, int (&kI)[2], int (&kJ)[2]) {
+                            const double djj_new, bool score, bool withV, Cand& pI, Cand& pJ, int (&kI)[2],
+                            int (&kJ)[2]) {
         double* Ai = a.A + (long long)i * a.lda;
         double* Aj = a.A + (long long)j * a.lda;
         const int cmin = min(i, j), cmax = max(i, j);
@@ -667,7 +668,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         for (int r = 0; r < MR; ++r) {
             int k = k0 + tid + r * NT;
             if (k >= k1) break;
-            if (a.V) {
+            if (withV && a.V) {
                 double* Vi = a.V + (long long)i * a.ldv;
                 double* Vj = a.V + (long long)j * a.ldv;
                 double vx = pvx[r], vy = pvy[r];
@@ -755,7 +756,40 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         }
     };
 
-    if (pivot == PJAC_PIVOT_CYCLIC) {
+    if (pivot == PJAC_PIVOT_RANDOM) {
+        // Sec. 4.2's comparator: the pair of every step is drawn, not
+        // selected; every CTA draws the same pair and computes the same
+        // rotation from the entries the last cluster barrier made visible
+        bool stop_now = false;
+        for (;;) {
+            if (rot % ce == 0) {
+                offdiag_check(stop_now);
+                if (stop_now) break;
+            }
+            if (rot >= a.max_rot) { status = PJAC_ENOCONV; break; }
+            int i, j;
+            random_pair(a.seed, rot, n, i, j);
+            const double q = ldcg(a.A + (long long)i * a.lda + j);
+            if (tid == 0) {
+                Rot rp = rot_params(diag[i], diag[j], q);
+                sh.c = rp.c; sh.s = rp.s;
+                sh.dii = __fma_rn(rp.t, q, diag[i]);
+                sh.djj = __fma_rn(-rp.t, q, diag[j]);
+            }
+            __syncthreads();
+            const double c = sh.c, s = sh.s, dii = sh.dii, djj = sh.djj;
+            __syncthreads();
+            if (tid == 0) { diag[i] = dii; diag[j] = djj; }
+            __syncthreads();
+            Cand d1 = no_cand(), d2 = no_cand();
+            int dk1[2] = {KEY_NONE, KEY_NONE}, dk2[2] = {KEY_NONE, KEY_NONE};
+            preload(i, j);
+            rotate_owned(i, j, c, s, dii, djj, false, true, d1, d2, dk1, dk2);
+            rot++;
+            cta_exchange_sync<CLUSTER>();
+        }
+        last_score = 0.0;
+    } else if (pivot == PJAC_PIVOT_CYCLIC) {
         bool stop_now = false;
         for (;;) {
             offdiag_check(stop_now);
@@ -782,7 +816,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     Cand d1 = no_cand(), d2 = no_cand();
                     int dk1[2] = {KEY_NONE, KEY_NONE}, dk2[2] = {KEY_NONE, KEY_NONE};
                     preload(i, j);
-                    rotate_owned(i, j, c, s, dii, djj, false, d1, d2, dk1, dk2);
+                    rotate_owned(i, j, c, s, dii, djj, false, true, d1, d2, dk1, dk2);
                     rot++;
                     any = true;
                     cta_exchange_sync<CLUSTER>();
@@ -816,8 +850,12 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         // the same winner in sh.sel and its rotation in pend_c, pend_s and
         // sh.t; the owners of rows i and j take those rows' new bests.
         // i, j < 0: no rows i, j (first selection).
+        // Between the cluster barrier's arrive and its wait every thread
+        // applies the rotation just made to its entries of V's columns i
+        // and j (loaded at the top of the step): the V update is off the
+        // path from one selection to the next.
         auto publish_select = [&](Cand loc, Cand pI, Cand pJ, const int (&kI)[2], const int (&kJ)[2], int i,
-                                  int j) {
+                                  int j, bool vupd, double vc, double vs) {
             if (tid < 3) {
                 Cand c = (tid == 0) ? loc : (tid == 1 ? pI : pJ);
                 double rd = 1.0, rq = 0.0, rt = 0.0;   // rot_cs: c = 1, s = 0
@@ -852,7 +890,22 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 }
             }
             SLAP(1);
-            cta_exchange_sync<CLUSTER>();
+            if (CLUSTER) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+            if (vupd && a.V) {
+                double* Vi = a.V + (long long)i * a.ldv;
+                double* Vj = a.V + (long long)j * a.ldv;
+#pragma unroll
+                for (int r = 0; r < MR; ++r) {
+                    const int k = k0 + tid + r * NT;
+                    if (k < k1) {
+                        const double vx = pvx[r], vy = pvy[r];
+                        Vi[k] = __fma_rn(vc, vx, __dmul_rn(vs, vy));
+                        Vj[k] = __fma_rn(vc, vy, -__dmul_rn(vs, vx));
+                    }
+                }
+            }
+            if (CLUSTER) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+            else __syncthreads();
             LAP(5);
             const int warp = tid >> 5, lane = tid & 31;
             int width = 1;
@@ -956,7 +1009,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             if (tid == 0) sh.tflag = 0;
             loc = block_select(loc, pivot, diag, sh);
             const int kn[2] = {KEY_NONE, KEY_NONE};
-            publish_select(loc, no_cand(), no_cand(), kn, kn, -1, -1);
+            publish_select(loc, no_cand(), no_cand(), kn, kn, -1, -1, false, 1.0, 0.0);
         }
         bool stop_now = false;
         for (;;) {
@@ -982,7 +1035,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             const double c = pend_c, s = pend_s, dii = diag[i], djj = diag[j];
             Cand pI = no_cand(), pJ = no_cand();
             int kI[2] = {KEY_NONE, KEY_NONE}, kJ[2] = {KEY_NONE, KEY_NONE};
-            rotate_owned(i, j, c, s, dii, djj, true, pI, pJ, kI, kJ);
+            rotate_owned(i, j, c, s, dii, djj, true, false, pI, pJ, kI, kJ);
             SLAP(4);
             rot++;
             __syncthreads();
@@ -1000,7 +1053,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             __syncthreads();
             LAP(3);
             if (tid == 0)
-                sh.tflag = (rank == 0 && a.budget_cycles > 0 && clock64() - start > a.budget_cycles) ? 1 : 0;
+                sh.tflag = (rank == 0 && a.budget_ns > 0 && (long long)(now_ns() - start) > a.budget_ns) ? 1 : 0;
             Cand loc = no_cand();
 #pragma unroll
             for (int r = 0; r < MR; ++r) {
@@ -1014,7 +1067,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             SLAP(2);
             cta_select3(loc, pI, pJ, pivot, diag, sh, kI, kJ, wb, cache, k0, k1);
             LAP(4);
-            publish_select(loc, pI, pJ, kI, kJ, i, j);
+            publish_select(loc, pI, pJ, kI, kJ, i, j, true, c, s);
             LAP(6);
         }
 #undef LAP
@@ -1081,7 +1134,7 @@ __global__ void __launch_bounds__(NT, MR == 1 ? 2 : 1) jacobi_batched_kernel(con
                                                            const int* order, int* counter,
                                                            int pivot, int stop, double tol,
                                                            long long max_rot_per_n2,
-                                                           long long budget_cycles) {
+                                                           long long budget_ns, unsigned long long seed) {
     __shared__ Sh sh;
     __shared__ int next;
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -1096,7 +1149,7 @@ __global__ void __launch_bounds__(NT, MR == 1 ? 2 : 1) jacobi_batched_kernel(con
         a.A = d.A; a.lda = d.n; a.V = d.V; a.ldv = d.n; a.Wd = d.Wd; a.n = d.n;
         a.pivot = pivot; a.stop = stop; a.tol = tol;
         a.max_rot = max_rot_per_n2 * (long long)d.n * (long long)d.n;
-        a.check_every = d.n; a.budget_cycles = budget_cycles; a.info = d.info;
+        a.check_every = d.n; a.budget_ns = budget_ns; a.info = d.info; a.seed = seed;
         double* diag = reinterpret_cast<double*>(dyn);
         Cand* cache = reinterpret_cast<Cand*>(diag + d.n);
         Cand* cache2 = cache + d.n;
@@ -1152,7 +1205,8 @@ cudaError_t launch_jacobi(const JacArgs& a, int P, cudaStream_t st) {
 template <int MR>
 static cudaError_t launch_batched_mr(const BatchDesc* d_desc, int nb, const int* d_order, int* d_counter,
                                      int pivot, int stop, double tol, long long max_rot_per_n2,
-                                     long long budget_cycles, size_t smem, int ctas, cudaStream_t st) {
+                                     long long budget_ns, size_t smem, int ctas, unsigned long long seed,
+                                     cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(jacobi_batched_kernel<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -1167,21 +1221,21 @@ static cudaError_t launch_batched_mr(const BatchDesc* d_desc, int nb, const int*
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     jacobi_batched_kernel<MR><<<ctas, NT, smem, st>>>(d_desc, nb, d_order, d_counter, pivot, stop, tol,
-                                                      max_rot_per_n2, budget_cycles);
+                                                      max_rot_per_n2, budget_ns, seed);
     return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_batched(const BatchDesc* d_desc, int nb, const int* d_order,
                                   int* d_counter, int pivot, int stop, double tol,
-                                  long long max_rot_per_n2, long long budget_cycles, int max_n,
-                                  int ctas, cudaStream_t st) {
+                                  long long max_rot_per_n2, long long budget_ns, int max_n,
+                                  int ctas, unsigned long long seed, cudaStream_t st) {
     if (max_n > NT * MAXR) return cudaErrorInvalidValue;
     size_t smem = jacobi_smem_bytes(max_n, 1);
     if (max_n <= NT)
         return launch_batched_mr<1>(d_desc, nb, d_order, d_counter, pivot, stop, tol, max_rot_per_n2,
-                                    budget_cycles, smem, ctas, st);
+                                    budget_ns, smem, ctas, seed, st);
     return launch_batched_mr<MAXR>(d_desc, nb, d_order, d_counter, pivot, stop, tol, max_rot_per_n2,
-                                   budget_cycles, smem, ctas, st);
+                                   budget_ns, smem, ctas, seed, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -16,7 +16,12 @@
 // Host code cannot use the array's name as a device address (in host code it
 // is only a host-side stand-in), so the device address is looked up once per
 // device with cudaGetSymbolAddress, with that device current, on the first
-// call made on that device.
+// call made on that device.  Under CUDA's lazy module loading that lookup is
+// also when the array is placed in device memory, and a kernel's first launch
+// is when its code is loaded: both take device memory.  So the first call on
+// a device does all of it at once -- the lookup and the loading of every
+// kernel the entry point launches -- and callers make that first call before
+// they reserve the device's memory.
 #include <cuda_runtime.h>
 #include <cstring>
 #include <mutex>
@@ -55,6 +60,11 @@ int scratch_address(void** out) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_err(e, "cudaGetSymbolAddress(scratch)");
+        // load the kernels this entry point launches (Jacobi, readout, input
+        // check, copies) now rather than at their first launch
+        e = preload_jacobi_kernels();
+        if (e == cudaSuccess) e = preload_gemm_kernels();
+        if (e != cudaSuccess) return cuda_err(e, "loading the kernels");
         g_addr[dev] = p;
     }
     *out = g_addr[dev];
@@ -120,8 +130,9 @@ extern "C" int pjac_solve_preconditioned_noalloc(double* A1, int n, int lda1, co
     a.tol = tol;
     a.max_rot = 50LL * n * (n - 1) / 2;
     a.check_every = n;
-    a.budget_cycles = (long long)(o.time_budget_s * 2.2e9);
+    a.budget_ns = (long long)(o.time_budget_s * 1e9);
     a.info = dinfo;
+    a.seed = o.seed;
     int P = jacobi_auto_cluster(n);
     while (P > 1 && (n + P - 1) / P < 8) P >>= 1;
     NK(launch_jacobi(a, P, st));

@@ -264,7 +264,7 @@ static int launch_lane(pjac_server* s, Lane& L) {
     if (batched) {
         r = pjac_solve_batched(L.h, nb, L.ns.data(), L.aoff.data(), L.dA, L.woff.data(), L.dW, L.aoff.data(),
                                L.dV, r0->pivot, r0->tol, L.dInfo, L.st);
-        if (r == PJAC_OK) s->launches += batched_launch_count();
+        if (r == PJAC_OK) s->launches += batched_launch_count(s->o.solver.no_precondition);
     } else {
         // single large request: asynchronous single-problem path
         r = solve_async_dev(L.h, L.dA, r0->n, r0->n, r0->pivot, r0->tol, L.dW, L.dV, r0->n, L.dInfo, L.st);
@@ -335,7 +335,7 @@ extern "C" int pjac_serve_submit(pjac_server* s, const double* A, int n, int lda
     if (!s || !A || !W || !ticket) return set_err(PJAC_EINVAL, "NULL argument");
     if (n < 2 || n > PJAC_MAX_N) return set_err(PJAC_EINVAL, "serve: n = %d outside [2, %d]", n, PJAC_MAX_N);
     if (lda < n || (V && ldv < n)) return set_err(PJAC_EINVAL, "serve: leading dimension < n");
-    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_CYCLIC) return set_err(PJAC_EINVAL, "bad pivot");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
     if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
     std::lock_guard<std::mutex> lk(s->mu);
     if ((int)s->q.waiting() >= s->o.max_queue)

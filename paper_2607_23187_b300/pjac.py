@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpjac.so")
 PJAC_OK, PJAC_PENDING = 0, 1
 PJAC_EINVAL, PJAC_ENOMEM, PJAC_EAGAIN = -1, -2, -3
 PJAC_ENOCONV, PJAC_ETIMEOUT, PJAC_ECUDA, PJAC_ENOTIMPL = -4, -5, -6, -7
-PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2}
+PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3}
 STOPS = {"offdiag": 0, "libound": 1}
 TRANSFORMS = {"split_bf16": 0, "fp64": 1}
 
@@ -33,7 +33,7 @@ EXPORTS = (
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
     "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
-    "pjac_product_launch_count",
+    "pjac_product_launch_count", "pjac_eig_lowprec",
 )
 
 
@@ -47,7 +47,9 @@ class Opts(ctypes.Structure):
     _fields_ = [("stop", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_rotations", ctypes.c_int64), ("check_every", ctypes.c_int64),
                 ("transform", ctypes.c_int), ("ns_steps", ctypes.c_int),
-                ("cluster_size", ctypes.c_int), ("time_budget_s", ctypes.c_double)]
+                ("cluster_size", ctypes.c_int), ("time_budget_s", ctypes.c_double),
+                ("no_precondition", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("refine_steps", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_solve_preconditioned.argtypes = [vp, vp, i, i, vp, i, i, d, vp, vp, i,
                                                 ctypes.POINTER(Info), vp]
         L.pjac_product.argtypes = [vp, i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]
+        L.pjac_eig_lowprec.argtypes = [vp, vp, i, i, vp, i, vp]
         L.pjac_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, i, d, vp, vp]
         L.pjac_serve_default_opts.argtypes = [ctypes.POINTER(ServeOpts)]
         L.pjac_serve_default_opts.restype = None
@@ -116,7 +119,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_status_string.restype = ctypes.c_char_p
         L.pjac_last_error.argtypes = []
         L.pjac_last_error.restype = ctypes.c_char_p
-        for name in ("pjac_create", "pjac_destroy", "pjac_set_opts", "pjac_precondition", "pjac_solve",
+        for name in ("pjac_create", "pjac_destroy", "pjac_set_opts", "pjac_precondition", "pjac_eig_lowprec",
+                     "pjac_solve",
                      "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_create",
                      "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
                      "pjac_serve_progress", "pjac_serve_get_stats"):
@@ -201,6 +205,16 @@ def pjac_precondition(h: Handle, a: torch.Tensor, q0: Optional[torch.Tensor] = N
     a1 = torch.empty((n, n), dtype=torch.float64, device=a.device)
     _check(load().pjac_precondition(h.h, _ptr(a), n, n, _ptr(q0c), _ptr(qt), n, _ptr(a1), n, _stream()))
     return qt.t(), a1
+
+
+def pjac_eig_lowprec(h: Handle, a: torch.Tensor) -> torch.Tensor:
+    """The low-precision spectral decomposition of Sec. 2.1 (FP32): returns
+    Q0 as an (n,n) FP32 tensor whose columns are eigenvector estimates."""
+    a = _sym_input(a)
+    n = a.shape[0]
+    q0t = torch.empty((n, n), dtype=torch.float32, device=a.device)
+    _check(load().pjac_eig_lowprec(h.h, _ptr(a), n, n, _ptr(q0t), n, _stream()))
+    return q0t.t()
 
 
 def pjac_product(h: Handle, a: torch.Tensor, b: torch.Tensor, trans_a: bool = False, trans_b: bool = False,

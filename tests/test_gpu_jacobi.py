@@ -238,3 +238,37 @@ def test_full_solve_known_spectrum(pj, h, cfg, n):
         assert np.linalg.norm(p.a @ V - V * w) / np.linalg.norm(p.a) <= 1e-12
         assert np.linalg.norm(V.T @ V - np.eye(p.n)) <= 1e-12
         assert info["off_rel"] <= 1e-15
+
+
+@pytest.mark.parametrize("n,cluster,seed", [(32, 1, 99), (300, 4, 7), (77, 2, 0)])
+def test_random_pivot_parity(pj, h, n, cluster, seed):
+    """Sec. 4.2's randomized comparator: both sides draw the same pairs from
+    the counter-based SplitMix64 sequence, so the results are bit-identical."""
+    if n == 32:
+        p, q0, q, a1 = preconditioned("cfg1")
+    elif n == 300:
+        p, q0, q, a1 = preconditioned("cfg2", n=300)
+    else:
+        rng = np.random.default_rng(21)
+        b = rng.standard_normal((77, 77))
+        a1, q = b + b.T, None
+    r, w, v = oracle_run(("rand", n, seed), a1, q, "random", 1e-15, seed=seed)
+    gw, gv, ga, info, st = gpu_run(pj, h, a1, q, "random", 1e-15, cluster_size=cluster, seed=seed)
+    assert st == 0 and r["status"] == 0
+    assert_bit_parity(r, w, v, gw, gv, ga, info)
+
+
+def test_solve_without_preconditioner(pj, h):
+    """opts.no_precondition: Algorithm 1 directly on A with V0 = I (the
+    setting of Sec. 4.2), bit-identical to the oracle on A itself."""
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((150, 150))
+    a = b @ b.T + 150 * np.eye(150)
+    a = 0.5 * (a + a.T)
+    r, w, v = oracle_run("noprec150", a, None, "gap", 1e-15)
+    h.set_opts(transform="fp64", no_precondition=1)
+    gw, gv, info, st = pj.pjac_solve(h, torch.tensor(a, device="cuda"), "gap", 1e-15)
+    h.set_opts(transform="fp64")
+    assert st == 0 and info["rotations"] == r["rotations"]
+    assert np.array_equal(gw.cpu().numpy(), w)
+    assert np.array_equal(gv.cpu().numpy(), v)
