@@ -61,7 +61,10 @@ typedef enum {
      * mod n, j' = (z div 2^32) mod (n-1), j = j' + [j' >= i], ordered.  A draw
      * with a_ij == 0 applies the identity and still counts as a rotation.
      * Off-diagonal stop only. */
-    PJAC_PIVOT_RANDOM = 3
+    PJAC_PIVOT_RANDOM = 3,
+    /* Sec. 4.2's relative score (1/a_ii + 1/a_jj) L_ij for positive definite
+     * matrices; pjac_svd_onesided only. */
+    PJAC_PIVOT_GAP_REL = 4
 } pjac_pivot;
 
 /* Stopping rules. */
@@ -267,6 +270,59 @@ int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_of
                        const double* A, const int64_t* w_off, double* W, const int64_t* v_off,
                        double* V, pjac_pivot pivot, double tol, pjac_info* infos, void* stream);
 
+/*
+ * One-sided Jacobi SVD with the paper's pivoting (Alg. 2) and the
+ * low-precision right-singular-vector preconditioner (Sec. 2.1, SVD
+ * paragraph).  B = U diag(S) V^T.
+ *   B   [in]  m x n, column-major, ldb >= m, 1 <= n <= m <= PJAC_MAX_N,
+ *             m <= 17458 with the split-BF16 products.  Not modified.
+ *   Vl  [in]  optional n x n FP32 right singular vectors of fl32(B)
+ *             (column-major, ldvl >= n).  NULL: computed on the device as
+ *             the FP32 eigenbasis of B^T B (see pjac_eig_lowprec).  Ignored
+ *             with opts.no_precondition (then V0 = I).
+ *   S   [out] n singular values, descending.
+ *   U   [out, nullable] m x n left singular vectors, ldu >= m (a column is
+ *             zero where its singular value is zero).
+ *   V   [out, nullable] n x n right singular vectors, ldv >= n.
+ * Steps: V0 = Newton--Schulz(Vl); B1 = B V0; A = B1^T B1 (symmetrised);
+ * Algorithm 1 on A with the given pivot rule and stop (each rotation makes
+ * columns i, j of B1 orthogonal as far as A records their inner products;
+ * A is updated two-sided and V0's columns rotated: the pivot rule sees
+ * (BV)^T BV as Sec. 2.1 prescribes); then the rotated B V is formed with
+ * one product, its column norms (scaled by a power of two) are the singular
+ * values.  Products use the handle's transform option.  Accuracy: absolute,
+ * about u ||B||^2 / sigma for each sigma (the Gram matrix is formed once).
+ * Synchronises the stream when info != NULL.  Returns like pjac_solve.
+ */
+int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, const float* Vl, int ldvl,
+             pjac_pivot pivot, double tol, double* S, double* U, int ldu, double* V, int ldv, pjac_info* info,
+             void* stream);
+
+/*
+ * One-sided Jacobi SVD for relative accuracy (Alg. 2 in the setting of
+ * Sec. 4.2: no preconditioner, the pivot matrix G = B^T B of the CURRENT
+ * columns).  G is formed once and, after each rotation (i,j), its rows and
+ * columns i and j are recomputed from the rotated columns, every entry a dot
+ * product summed in row order with fused multiply-adds.  The rotation is the
+ * one that makes columns i, j orthogonal as G records them.  Pivot rules:
+ *   PJAC_PIVOT_GAP_REL  Sec. 4.2's (1/g_ii + 1/g_jj) L_ij; stop when the
+ *                       largest score is <= tol (a relative bound),
+ *   PJAC_PIVOT_GAP      Eq. (1.1) on G; stop at largest score <= tol ||G0||_F,
+ *   PJAC_PIVOT_GREEDY   |g_ij|; stop at largest score <= tol ||G0||_F,
+ *   PJAC_PIVOT_RANDOM   uniform pairs (Sec. 4.2's comparator); stop tested
+ *                       every n draws on the GAP_REL scores.
+ * Rotation budget: opts.max_rotations (0: 50 n(n-1)/2) -> PJAC_ENOCONV.
+ *   B   [in]  m x n, ldb >= m, 2 <= n <= 1024, n <= m <= PJAC_MAX_N; not
+ *             modified.
+ *   S   [out] n singular values sqrt(g_kk) of the final G, descending.
+ *   U   [out, nullable] m x n, ldu >= m: the rotated columns / S.
+ *   V   [out, nullable] n x n, ldv >= n: the accumulated rotations.
+ * One CTA runs the iteration (the dependent chain of this small, accurate
+ * form); O(mn) work per rotation.  Synchronises the stream when info != NULL.
+ */
+int pjac_svd_onesided(pjac_handle* h, const double* B, int m, int n, int ldb, pjac_pivot pivot, double tol,
+                      double* S, double* U, int ldu, double* V, int ldv, pjac_info* info, void* stream);
+
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of eigenproblems of mixed sizes.  Requests
  * are admitted while their device footprint fits the memory budget and a
@@ -345,6 +401,13 @@ int pjac_solve_launch_count(pjac_handle* h, int n);
  * one).  Returns -1 when h is NULL, a size is out of range, or the split
  * product does not support the shape. */
 int pjac_product_launch_count(pjac_handle* h, int m, int n, int k);
+
+/* Measured FP64 fused multiply-add rate of the current device in TFLOP/s
+ * (2 flops per FMA): eight independent chains per thread over a grid of
+ * eight CTAs of 256 threads per SM, timed with CUDA events on the stream
+ * after one warm-up launch.  A diagnostic for the roofline of the FP64-bound
+ * kernels.  Synchronises the stream. */
+int pjac_probe_fp64(double* tflops, void* stream);
 
 /* Human-readable text for a status code (static storage). */
 const char* pjac_status_string(int status);

@@ -34,7 +34,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3}
+PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3, "gap_rel": 4}
 STOPS = {"offdiag": 0, "libound": 1}
 
 
@@ -89,6 +89,13 @@ def lib():
                                     ctypes.c_uint64, ctypes.POINTER(_Info)]
             L.or_splitmix64.restype = ctypes.c_uint64
             L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.or_gap_rel_score.restype = ctypes.c_double
+            L.or_gap_rel_score.argtypes = [ctypes.c_double] * 3
+            L.or_svd_onesided.restype = ctypes.c_int
+            L.or_svd_onesided.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_int)]
             L.or_random_pair.restype = None
             L.or_random_pair.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -377,3 +384,104 @@ def jacobi_many(mats, pivot: str = "gap", stop: str = "offdiag", tol: float = 1e
     outa = [A[o:o + s].reshape(m, m) for o, s, m in zip(off, sizes, ns)]
     outv = [V[o:o + s].reshape(m, m) for o, s, m in zip(off, sizes, ns)]
     return outa, outv, rots, st
+
+
+# ----------------------------------------------------------------------------
+# Alg. 2 with Sec. 2.1's SVD preconditioner: one-sided Jacobi SVD
+# ----------------------------------------------------------------------------
+def right_vectors_fp32(b: np.ndarray) -> np.ndarray:
+    """Low-precision right singular vectors V_l of B (Sec. 2.1, SVD
+    paragraph, u_l = single): LAPACK's FP32 SVD of fl32(B)."""
+    _, _, vt = np.linalg.svd(np.asarray(b, dtype=np.float32), full_matrices=False)
+    return np.ascontiguousarray(vt.T.astype(np.float32))
+
+
+def column_norms(x: np.ndarray) -> np.ndarray:
+    """||x_k||_2 of every column, each summed in row order after scaling by
+    the exact power of two 2^-e, e = ilogb(max_r |x_rk|), so that squares
+    neither overflow nor underflow."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(x.shape[1])
+    for k in range(x.shape[1]):
+        m = np.max(np.abs(x[:, k]))
+        if m == 0.0:
+            continue
+        e = int(np.frexp(m)[1]) - 1
+        acc = 0.0
+        for v in np.ldexp(x[:, k], -e):
+            acc += v * v
+        out[k] = np.ldexp(np.sqrt(acc), e)
+    return out
+
+
+def svd_jacobi(b: np.ndarray, pivot: str = "gap", tol: float = 1e-15, vl: Optional[np.ndarray] = None,
+               precondition_vectors: bool = True, ns_steps: int = 3, **kw) -> Dict:
+    """One-sided Jacobi SVD of B (m x n, m >= n) with the paper's pivoting
+    (Alg. 2; Sec. 2.1's SVD paragraph).
+
+    Preconditioner: V_l, the FP32 right singular vectors (``vl`` or
+    ``right_vectors_fp32``), made orthogonal by Newton--Schulz: V.  Jacobi
+    then runs on B1 = BV, whose columns are orthogonal up to O(u_l ||B||).
+    As Sec. 2.1 prescribes, the pivot rule is applied to A = (BV)^T BV: each
+    rotation (c, s) is the one that makes columns i, j of B1 orthogonal as
+    far as A records their inner products, A is updated two-sided
+    (A <- G^T A G, exactly Algorithm 1) and the same rotation multiplies the
+    columns of V.  The rotated matrix B1 G_1 G_2 ... equals B V_final, which
+    is formed once at the end; the singular values are its column norms,
+    sorted descending, U its normalised columns.  Without the preconditioner
+    V = I.  Returns sigma, U, V (columns in sigma's order), rotations,
+    status and the final A.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    m, n = b.shape
+    if precondition_vectors:
+        if vl is None:
+            vl = right_vectors_fp32(b)
+        v0 = reorth_ns(vl, ns_steps)
+    else:
+        v0 = np.eye(n)
+    b1 = b @ v0
+    a = b1.T @ b1
+    a = 0.5 * (a + a.T)
+    r = jacobi(a, v0, pivot=pivot, tol=tol, **kw)
+    bf = b @ r["v"]
+    sig = column_norms(bf)
+    order = np.argsort(-sig, kind="stable")
+    sig = sig[order]
+    v = r["v"][:, order]
+    u = bf[:, order] / np.where(sig > 0, sig, 1.0)[None, :]
+    r.update({"sigma": sig, "u": u, "v_sorted": v, "v0": v0, "a0": a})
+    return r
+
+
+def gap_rel_score(aii: float, ajj: float, aij: float) -> float:
+    """Sec. 4.2's relative score (1/a_ii + 1/a_jj) L_ij for SPD matrices."""
+    return lib().or_gap_rel_score(float(aii), float(ajj), float(aij))
+
+
+def svd_onesided(b: np.ndarray, pivot: str = "gap_rel", tol: float = 1e-15,
+                 max_rot: Optional[int] = None, seed: int = 0) -> Dict:
+    """One-sided Jacobi SVD with the inner products recomputed from the
+    rotated columns after every rotation (Alg. 2; Sec. 4.2's setting, no
+    preconditioner); see ``or_svd_onesided``.  Returns sigma (descending,
+    sqrt of the final Gram diagonal), U (normalised columns), V, rotations,
+    status, and the final B and Gram matrix."""
+    b = np.asarray(b, dtype=np.float64)
+    m, n = b.shape
+    bc = np.asfortranarray(b).copy(order="F")
+    v = np.eye(n)                      # column k at v[:, k]: Fortran order
+    v = np.asfortranarray(v)
+    g = np.zeros((n, n))
+    if max_rot is None:
+        max_rot = 50 * n * (n - 1) // 2 + 1
+    rot = ctypes.c_longlong(0)
+    st = ctypes.c_int(0)
+    lib().or_svd_onesided(bc.ctypes.data_as(ctypes.c_void_p), m, n, v.ctypes.data_as(ctypes.c_void_p),
+                          PIVOTS[pivot], float(tol), int(max_rot), ctypes.c_uint64(seed), _ptr(g),
+                          ctypes.byref(rot), ctypes.byref(st))
+    sig_u = np.sqrt(np.maximum(np.diag(g), 0.0))
+    order = np.argsort(-sig_u, kind="stable")
+    sig = sig_u[order]
+    u = bc[:, order] / np.where(sig > 0, sig, 1.0)[None, :]
+    return {"sigma": sig, "u": u, "v": np.ascontiguousarray(v[:, order]), "rotations": int(rot.value),
+            "status": int(st.value), "b": np.ascontiguousarray(bc), "g": g, "order": order}

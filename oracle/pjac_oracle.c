@@ -454,3 +454,141 @@ int or_jacobi_many(int count, const int* ns, const long long* a_off, double* A,
     }
     return err;
 }
+
+/* ------------------------------------------------------------------------
+ * One-sided Jacobi SVD with inner products recomputed from the columns
+ * (Alg. 2, and Sec. 4.2's relative-accuracy setting: no preconditioner).
+ *
+ * B is m x n column-major (column k at B + k*m), overwritten by B G_1 G_2 ...
+ * The pivot matrix is the Gram matrix G = B^T B of the CURRENT columns:
+ * g_kl = sum_r b_rk b_rl, accumulated in row order with fma.  It is formed
+ * once in full; after each rotation (i,j) the rows/columns i and j of G are
+ * recomputed from the rotated columns (every other entry is unchanged).
+ *   Rotation: (c, s, t) of or_rotation on (g_ii, g_jj, g_ij), which makes
+ *   columns i, j orthogonal as far as G records them; b_i' = fma(c,b_i,s*b_j),
+ *   b_j' = fma(c,b_j,-(s*b_i)), the same for V's columns.
+ *   Scores: GAP, Eq. (1.1) on G; GREEDY |g_ij|; GAP_REL, Sec. 4.2's
+ *   L^_ij = (1/g_ii + 1/g_jj) L_ij (0 when g_ii or g_jj is 0); RANDOM, the
+ *   uniform comparator of Sec. 4.2 (or_random_pair).  Ties: smallest (i,j).
+ *   Stop (status 0): the largest score is <= tol (GAP_REL: a relative
+ *   bound; GAP, GREEDY: tol * ||G0||_F), tested before every rotation for
+ *   the greedy-type rules and every n draws for RANDOM (on GAP_REL scores).
+ *   Budget: max_rot rotations (status 1).
+ * The singular values are sqrt(g_kk) of the final G; the caller sorts them.
+ * ------------------------------------------------------------------------ */
+#define OR_PIVOT_GAP_REL 4
+
+static double or_dot(const double* x, const double* y, int m) {
+    double acc = 0.0;
+    for (int r = 0; r < m; ++r) acc = fma(x[r], y[r], acc);
+    return acc;
+}
+
+/* Sec. 4.2's relative score. */
+double or_gap_rel_score(double aii, double ajj, double aij) {
+    if (aij == 0.0 || aii == 0.0 || ajj == 0.0) return 0.0;
+    return (1.0 / aii + 1.0 / ajj) * or_gap_score(aii, ajj, aij);
+}
+
+static double or_os_score(int pivot, const double* G, int n, int k, int l) {
+    double gkl = G[(size_t)k * n + l];
+    if (pivot == OR_PIVOT_GREEDY) return fabs(gkl);
+    double gkk = G[(size_t)k * n + k], gll = G[(size_t)l * n + l];
+    if (pivot == OR_PIVOT_GAP) return or_gap_score(gkk, gll, gkl);
+    return or_gap_rel_score(gkk, gll, gkl);
+}
+
+static void or_os_rescan(int pivot, const double* G, int n, int k, double* bv, int* bc) {
+    double best = -1.0;
+    int col = (k == 0) ? 1 : 0;
+    for (int l = 0; l < n; ++l) {
+        if (l == k) continue;
+        double v = or_os_score(pivot, G, n, k, l);
+        if (v > best) { best = v; col = l; }
+    }
+    bv[k] = best;
+    bc[k] = col;
+}
+
+int or_svd_onesided(double* B, int m, int n, double* V, int pivot, double tol, long long max_rot,
+                    uint64_t seed, double* G, long long* rot_out, int* status_out) {
+    for (int k = 0; k < n; ++k)
+        for (int l = 0; l <= k; ++l) {
+            double g = or_dot(B + (size_t)k * m, B + (size_t)l * m, m);
+            G[(size_t)k * n + l] = g;
+            G[(size_t)l * n + k] = g;
+        }
+    double normg = or_frobenius(G, n);
+    int score_pivot = (pivot == OR_PIVOT_RANDOM) ? OR_PIVOT_GAP_REL : pivot;
+    double thr = (score_pivot == OR_PIVOT_GAP_REL) ? tol : tol * normg;
+    double* bv = (double*)malloc(sizeof(double) * (size_t)n);
+    int* bc = (int*)malloc(sizeof(int) * (size_t)n);
+    for (int k = 0; k < n; ++k) or_os_rescan(score_pivot, G, n, k, bv, bc);
+    long long rot = 0;
+    int status = 1;
+    for (;;) {
+        int i, j;
+        if (pivot == OR_PIVOT_RANDOM) {
+            if (rot % n == 0) {
+                double mx = 0.0;
+                for (int k = 0; k < n; ++k) mx = fmax(mx, bv[k]);
+                if (mx <= thr) { status = 0; break; }
+            }
+            if (rot >= max_rot) break;
+            or_random_pair(seed, rot, n, &i, &j);
+        } else {
+            double best = -1.0;
+            int bk = 0;
+            for (int k = 0; k < n; ++k)
+                if (bv[k] > best) { best = bv[k]; bk = k; }
+            if (best <= thr || best == 0.0) { status = 0; break; }
+            if (rot >= max_rot) break;
+            i = bk < bc[bk] ? bk : bc[bk];
+            j = bk < bc[bk] ? bc[bk] : bk;
+        }
+        double c, s, t;
+        or_rotation(G[(size_t)i * n + i], G[(size_t)j * n + j], G[(size_t)i * n + j], &c, &s, &t);
+        double* bi = B + (size_t)i * m;
+        double* bj = B + (size_t)j * m;
+        for (int r = 0; r < m; ++r) {
+            double x = bi[r], y = bj[r];
+            bi[r] = fma(c, x, s * y);
+            bj[r] = fma(c, y, -(s * x));
+        }
+        if (V) {
+            double* vi = V + (size_t)i * n;
+            double* vj = V + (size_t)j * n;
+            for (int r = 0; r < n; ++r) {
+                double x = vi[r], y = vj[r];
+                vi[r] = fma(c, x, s * y);
+                vj[r] = fma(c, y, -(s * x));
+            }
+        }
+        /* rows and columns i, j of G from the rotated columns */
+        for (int k = 0; k < n; ++k) {
+            double gi = or_dot(bi, B + (size_t)k * m, m);
+            double gj = or_dot(bj, B + (size_t)k * m, m);
+            G[(size_t)i * n + k] = gi; G[(size_t)k * n + i] = gi;
+            G[(size_t)j * n + k] = gj; G[(size_t)k * n + j] = gj;
+        }
+        rot++;
+        /* row-best cache (Sec. 3.2), as or_update_cache */
+        for (int k = 0; k < n; ++k) {
+            if (k == i || k == j || bc[k] == i || bc[k] == j) {
+                or_os_rescan(score_pivot, G, n, k, bv, bc);
+                continue;
+            }
+            int cols[2] = {i, j};
+            for (int q = 0; q < 2; ++q) {
+                int l = cols[q];
+                double v = or_os_score(score_pivot, G, n, k, l);
+                if (or_better(v, k, l, bv[k], k, bc[k])) { bv[k] = v; bc[k] = l; }
+            }
+        }
+    }
+    free(bv);
+    free(bc);
+    *rot_out = rot;
+    *status_out = status;
+    return 0;
+}

@@ -63,6 +63,7 @@ struct pjac_handle {
     int device;
     DevBuf ws;          // main workspace
     DevBuf tcws;        // tensor-core product workspace
+    DevBuf svdws;       // SVD: the m x n rotated matrix
     int coop_cap = 0;   // cap of the cooperative grids (0: the whole GPU)
     cudaEvent_t ev[4];
     std::mutex mu;
@@ -140,6 +141,7 @@ extern "C" int pjac_destroy(pjac_handle* h) {
     pjac_batched_release(h);
     h->ws.release();
     h->tcws.release();
+    h->svdws.release();
     for (int k = 0; k < 4; ++k) cudaEventDestroy(h->ev[k]);
     delete h;
     return PJAC_OK;
@@ -286,11 +288,14 @@ static int newton_schulz(pjac_handle* h, double* Q, long long ldq, int n, int st
 // its many rotation layers, in the eigenvectors and in orthogonality (each
 // FP32 rotation moves column norms by a rounding unit).  So: X = fl64(Q0)
 // made orthogonal (Newton--Schulz), then a refinement pass on
-// B = X^T fl32(A) X that diagonalises it further, X <- X (I + D).
+// B = X^T fl32(A) X that diagonalises it further, X <- X (I + D).  With
+// fp32_refine == false that pass is left out: the caller's FP64 first-order
+// refinement steps (pjac_opts.refine_steps) do its work.
 static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, double* Q, long long ldq,
-                         SolveWs& w, cudaStream_t st) {
+                         SolveWs& w, cudaStream_t st, bool fp32_refine = true) {
     CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, h->coop_cap, st));
     CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
+    if (!fp32_refine) return PJAC_OK;
     int r = newton_schulz(h, Q, ldq, n, 2, w, st);
     if (r) return r;
     CK(round_to_fp32(A, lda, w.Y, n, n, st));                             // Y = fl32(A)
@@ -308,21 +313,34 @@ static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, 
 }
 
 // One first-order refinement step of (A1, Q) (pjac_opts.refine_steps, an
-// extension beyond the paper): Z = I + s D from A1, made orthogonal by
-// Newton--Schulz, then A1 <- Z^T A1 Z (symmetrised) and Q <- Q Z.
+// extension beyond the paper): Z = I + E with E = s D from A1, made
+// orthogonal by Newton--Schulz, then A1 <- Z^T A1 Z (symmetrised) and
+// Q <- Q Z.  Everything is written in terms of the small E, so that each
+// product's error is relative to |E| rather than to |Z| ~ 1:
+//   R = E^T E + E + E^T,  E <- E - R/2 - E R/2              (Newton--Schulz)
+//   T = A1 E,  A1 <- A1 + (T + T^T + E^T T),  Q <- Q + Q E.
 static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, long long ldq, int n, SolveWs& w,
                        cudaStream_t st) {
-    CK(refine_build(A1, lda1, n, REFINE_TAU, w.Z, w.maxsum, REFINE_MAX_ROWSUM, st));
-    int r = newton_schulz(h, w.Z, n, n, REFINE_NS_STEPS, w, st);
+    double* E = w.Z;
+    CK(refine_build(A1, lda1, n, REFINE_TAU, E, w.maxsum, REFINE_MAX_ROWSUM, st));
+    int r;
+    for (int it = 0; it < REFINE_NS_STEPS; ++it) {
+        r = product(h, true, false, n, 1.0, E, n, E, n, 0.0, w.Y, n, st);         // Y = E^T E
+        if (r) return r;
+        CK(refine_r(w.Y, E, n, st));                                               // R = Y + E + E^T
+        r = product(h, false, false, n, -0.5, E, n, w.Y, n, 0.0, w.T, n, st);     // T = -E R / 2
+        if (r) return r;
+        CK(refine_ns(E, w.Y, w.T, n, st));                                         // E <- E - R/2 + T
+    }
+    r = product(h, false, false, n, 1.0, A1, lda1, E, n, 0.0, w.T, n, st);       // T = A1 E
     if (r) return r;
-    r = product(h, false, false, n, 1.0, A1, lda1, w.Z, n, 0.0, w.T, n, st);   // T = A1 Z
+    r = product(h, true, false, n, 1.0, E, n, w.T, n, 0.0, w.Y, n, st);          // Y = E^T T
     if (r) return r;
-    r = product(h, true, false, n, 1.0, w.Z, n, w.T, n, 0.0, A1, lda1, st);   // A1 = Z^T T
-    if (r) return r;
+    CK(refine_a1(A1, lda1, w.T, w.Y, n, st));
     CK(symmetrize(A1, lda1, n, st));
-    r = product(h, false, false, n, 1.0, Q, ldq, w.Z, n, 0.0, w.T, n, st);     // T = Q Z
+    r = product(h, false, false, n, 1.0, Q, ldq, E, n, 0.0, w.T, n, st);         // T = Q E
     if (r) return r;
-    CK(copy_f64(w.T, n, Q, ldq, n, n, st));
+    CK(add_f64(Q, ldq, w.T, n, n, st));                                          // Q <- Q + T
     return PJAC_OK;
 }
 
@@ -337,8 +355,9 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
     } else {
         // after the final reorthogonalisation below, fl32(A) = Q Lambda Q^T
-        // to FP32 accuracy
-        int r = lowprec_basis(h, A, n, lda, Q, ldq, w, st);
+        // to FP32 accuracy (with refinement steps requested, those take the
+        // place of the FP32 refinement pass)
+        int r = lowprec_basis(h, A, n, lda, Q, ldq, w, st, h->opts.refine_steps == 0);
         if (r) return r;
     }
     int r = newton_schulz(h, Q, ldq, n, h->opts.ns_steps, w, st);
@@ -599,6 +618,130 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
     return finish_info(h, w.info, info, st, true);
 }
 
+extern "C" int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, const float* Vl, int ldvl,
+                        pjac_pivot pivot, double tol, double* S, double* U, int ldu, double* V, int ldv,
+                        pjac_info* info, void* stream) {
+    if (!h || !B || !S) return set_err(PJAC_EINVAL, "NULL argument");
+    if (n < 1 || m < n || m > PJAC_MAX_N) return set_err(PJAC_EINVAL, "need 1 <= n <= m <= %d (m = %d, n = %d)",
+                                                           PJAC_MAX_N, m, n);
+    if (ldb < m || (U && ldu < m) || (V && ldv < n) || (Vl && ldvl < n))
+        return set_err(PJAC_EINVAL, "leading dimension too small");
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    if (h->opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
+        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveWs w;
+    int r = layout_ws(h, n, &w, st);
+    if (r) return r;
+    r = h->svdws.ensure(align256((size_t)m * n * 8), st);
+    if (r) return r;
+    double* BF = static_cast<double*>(h->svdws.p);
+    CK(check_finite_rect(B, ldb, m, n, w.flag, st));
+    {
+        int hflag = 0;
+        CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hflag) return set_err(PJAC_EINVAL, "input contains NaN or Inf");
+    }
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16) {
+        size_t need = 0;
+        const int shapes[3][3] = {{m, n, n}, {n, n, m}, {n, n, n}};
+        for (const auto& sh : shapes) {
+            size_t b = gemm_split_bf16_ws(sh[0], sh[1], sh[2]);
+            if (b == 0) return set_err(PJAC_ENOTIMPL, "split-BF16 product not available for m = %d", m);
+            need = need > b ? need : b;
+        }
+        r = h->tcws.ensure(need, st);
+        if (r) return r;
+        CK(cudaMemsetAsync(gemm_split_bf16_errflag(h->tcws.p), 0, sizeof(int), st));
+    }
+    CK(cudaEventRecord(h->ev[0], st));
+    // V0: Newton--Schulz of the low-precision right singular vectors
+    if (h->opts.no_precondition) {
+        CK(set_identity(w.Vw, n, n, st));
+    } else {
+        if (Vl) {
+            CK(copy_f32_to_f64(Vl, ldvl, w.Vw, n, n, st));
+        } else {
+            // FP32 eigenbasis of G = B^T B (its eigenvectors are B's right
+            // singular vectors)
+            r = product_mnk(h, true, false, n, n, m, 1.0, B, ldb, B, ldb, 0.0, w.A1, n, st);
+            if (r) return r;
+            CK(symmetrize(w.A1, n, n, st));
+            r = lowprec_basis(h, w.A1, n, n, w.Vw, n, w, st, h->opts.refine_steps == 0);
+            if (r) return r;
+        }
+        r = newton_schulz(h, w.Vw, n, n, h->opts.ns_steps, w, st);
+        if (r) return r;
+    }
+    CK(cudaEventRecord(h->ev[1], st));
+    // B1 = B V0, A = B1^T B1
+    r = product_mnk(h, false, false, m, n, n, 1.0, B, ldb, w.Vw, n, 0.0, BF, m, st);
+    if (r) return r;
+    r = product_mnk(h, true, false, n, n, m, 1.0, BF, m, BF, m, 0.0, w.A1, n, st);
+    if (r) return r;
+    CK(symmetrize(w.A1, n, n, st));
+    for (int k = 0; k < h->opts.refine_steps; ++k) {
+        r = refine_step(h, w.A1, n, w.Vw, n, n, w, st);
+        if (r) return r;
+    }
+    CK(cudaEventRecord(h->ev[2], st));
+    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    if (r) return r;
+    // the rotated matrix B V, its column norms, the sorted factors
+    r = product_mnk(h, false, false, m, n, n, 1.0, B, ldb, w.Vw, n, 0.0, BF, m, st);
+    if (r) return r;
+    CK(launch_svd_readout(BF, m, m, w.Vw, n, n, w.Wd, w.rank, S, U, ldu, V, ldv, st));
+    if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16)
+        CK(gemm_split_bf16_fold_status(h->tcws.p, w.info, st));
+    CK(cudaEventRecord(h->ev[3], st));
+    if (!info) return PJAC_OK;
+    return finish_info(h, w.info, info, st, true);
+}
+
+extern "C" int pjac_svd_onesided(pjac_handle* h, const double* B, int m, int n, int ldb, pjac_pivot pivot,
+                                 double tol, double* S, double* U, int ldu, double* V, int ldv, pjac_info* info,
+                                 void* stream) {
+    if (!h || !B || !S) return set_err(PJAC_EINVAL, "NULL argument");
+    if (n < 2 || n > 1024 || m < n || m > PJAC_MAX_N)
+        return set_err(PJAC_EINVAL, "need 2 <= n <= 1024 and n <= m <= %d (m = %d, n = %d)", PJAC_MAX_N, m, n);
+    if (ldb < m || (U && ldu < m) || (V && ldv < n)) return set_err(PJAC_EINVAL, "leading dimension too small");
+    if (pivot != PJAC_PIVOT_GAP_REL && pivot != PJAC_PIVOT_GAP && pivot != PJAC_PIVOT_GREEDY &&
+        pivot != PJAC_PIVOT_RANDOM)
+        return set_err(PJAC_EINVAL, "pjac_svd_onesided: pivot must be GAP_REL, GAP, GREEDY or RANDOM");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveWs w;
+    int r = layout_ws(h, n, &w, st);
+    if (r) return r;
+    r = h->svdws.ensure(align256((size_t)m * n * 8), st);
+    if (r) return r;
+    double* Bw = static_cast<double*>(h->svdws.p);
+    CK(check_finite_rect(B, ldb, m, n, w.flag, st));
+    {
+        int hflag = 0;
+        CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hflag) return set_err(PJAC_EINVAL, "input contains NaN or Inf");
+    }
+    CK(cudaEventRecord(h->ev[0], st));
+    CK(cudaEventRecord(h->ev[1], st));
+    CK(copy_f64(B, ldb, Bw, m, m, n, st));
+    CK(set_identity(w.Vw, n, n, st));
+    CK(cudaEventRecord(h->ev[2], st));
+    long long pairs = (long long)n * (n - 1) / 2;
+    long long max_rot = h->opts.max_rotations > 0 ? h->opts.max_rotations : 50 * pairs;
+    CK(launch_svd_onesided(Bw, m, n, w.Vw, w.A1, (int)pivot, tol, max_rot, h->opts.seed, budget_ns(h->opts),
+                           w.info, st));
+    CK(launch_os_readout(w.A1, Bw, m, w.Vw, n, w.Wd, w.rank, S, U, ldu, V, ldv, st));
+    CK(cudaEventRecord(h->ev[3], st));
+    if (!info) return PJAC_OK;
+    return finish_info(h, w.info, info, st, true);
+}
+
 extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     if (!h || n < 1 || n > PJAC_MAX_N) return -1;
     if (n == 1) return 0;
@@ -614,12 +757,15 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     // two products, 3I - Y and a copy per step
     c += (2 + ns) * (2 * P + 2);
     // fl32(A), T = fl32(A) X, B = X^T T, symmetrise, refinement, copy, X D, add
-    c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
+    // (left out when FP64 refinement steps take the FP32 refinement's place)
+    if (h->opts.refine_steps == 0) c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
+    else c -= 2 * (2 * P + 2);
     // transform (two products) and symmetrise, Jacobi, readout (two kernels)
     c += 2 * P + 1 + 1 + 2;
-    // refinement steps: build and scale, Newton--Schulz, three products,
-    // symmetrise, copy
-    c += h->opts.refine_steps * (2 + REFINE_NS_STEPS * (2 * P + 2) + 3 * P + 2);
+    // refinement steps: build and scale, Newton--Schulz (two products and
+    // two element-wise steps each), three products, the A1 update,
+    // symmetrise, the Q update
+    c += h->opts.refine_steps * (2 + REFINE_NS_STEPS * (2 * P + 2) + 3 * P + 3);
     if (split) c += 1;  // product status folded into the solve record
     return c;
 }

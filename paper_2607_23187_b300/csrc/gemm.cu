@@ -190,16 +190,60 @@ __global__ void refine_build_kernel(const double* A1, long long lda1, int n, dou
     }
 }
 
-// Z <- I + s D with s = min(1, limit / max row sum).
+// E <- s D with s = min(1, limit / max row sum)  (Z = I + E).
 __global__ void refine_scale_kernel(double* Z, int n, const unsigned long long* maxsum, double limit) {
     const double m = __longlong_as_double((long long)*maxsum);
     const double s = (m > limit) ? __ddiv_rn(limit, m) : 1.0;
     const long long nn = (long long)n * n;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x)
+        Z[e] = __dmul_rn(s, Z[e]);
+}
+
+// The refinement works on E = Z - I, so that every product involves only
+// the small E (and the split product's error, relative to the operands'
+// row and column scales, stays relative to |E|).
+// R = E^T E + E + E^T: Y holds E^T E on entry.
+__global__ void refine_r_kernel(double* Y, const double* E, int n) {
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e % n), c = (int)(e / n);
-        Z[e] = (r == c) ? 1.0 : __dmul_rn(s, Z[e]);
+        Y[e] = __dadd_rn(Y[e], __dadd_rn(E[e], E[(long long)r * n + c]));
     }
+}
+
+// Newton--Schulz on Z = I + E, Z <- Z (I - R/2): E <- E - R/2 + T with
+// T = -E R / 2 on entry.
+__global__ void refine_ns_kernel(double* E, const double* R, const double* T, int n) {
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x)
+        E[e] = __dadd_rn(E[e], __dadd_rn(__dmul_rn(-0.5, R[e]), T[e]));
+}
+
+// Z^T A1 Z = A1 + (T + T^T + E^T T) with T = A1 E; Y holds E^T T.
+__global__ void refine_a1_kernel(double* A1, long long lda1, const double* T, const double* Y, int n) {
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % n), c = (int)(e / n);
+        const double d = __dadd_rn(__dadd_rn(T[e], T[(long long)r * n + c]), Y[e]);
+        A1[(long long)c * lda1 + r] = __dadd_rn(A1[(long long)c * lda1 + r], d);
+    }
+}
+
+cudaError_t refine_r(double* Y, const double* E, int n, cudaStream_t st) {
+    refine_r_kernel<<<592, 256, 0, st>>>(Y, E, n);
+    return cudaGetLastError();
+}
+cudaError_t refine_ns(double* E, const double* R, const double* T, int n, cudaStream_t st) {
+    refine_ns_kernel<<<592, 256, 0, st>>>(E, R, T, n);
+    return cudaGetLastError();
+}
+cudaError_t refine_a1(double* A1, long long lda1, const double* T, const double* Y, int n, cudaStream_t st) {
+    refine_a1_kernel<<<592, 256, 0, st>>>(A1, lda1, T, Y, n);
+    return cudaGetLastError();
 }
 
 cudaError_t refine_build(const double* A1, long long lda1, int n, double tau, double* Z,
@@ -309,6 +353,9 @@ cudaError_t preload_gemm_kernels() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, copy_f64_f32_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_build_kernel);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_scale_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_r_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_ns_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, refine_a1_kernel);
     return e;
 }
 

@@ -86,6 +86,9 @@ constexpr double REFINE_MAX_ROWSUM = 0.25;
 constexpr int REFINE_NS_STEPS = 5;
 cudaError_t refine_build(const double* A1, long long lda1, int n, double tau, double* Z,
                          unsigned long long* maxsum, double limit, cudaStream_t st);
+cudaError_t refine_r(double* Y, const double* E, int n, cudaStream_t st);
+cudaError_t refine_ns(double* E, const double* R, const double* T, int n, cudaStream_t st);
+cudaError_t refine_a1(double* A1, long long lda1, const double* T, const double* Y, int n, cudaStream_t st);
 cudaError_t three_i_minus(double* Y, long long ldy, int n, cudaStream_t st);
 cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cudaStream_t st);
 
@@ -110,6 +113,20 @@ cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_
 void handle_set_coop_cap(pjac_handle* h, int max_grid);
 cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st);
 cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st);
+
+// svd.cu: readout of the one-sided Jacobi SVD
+cudaError_t check_finite_rect(const double* A, long long lda, int m, int n, int* d_flag, cudaStream_t st);
+cudaError_t launch_svd_readout(const double* BF, long long ldbf, int m, const double* Vw, long long ldvw, int n,
+                               double* sig, int* rank, double* S, double* U, long long ldu, double* V,
+                               long long ldv, cudaStream_t st);
+cudaError_t preload_svd_kernels();
+cudaError_t launch_svd_onesided(double* B, int m, int n, double* V, double* G, int pivot, double tol,
+                                long long max_rot, unsigned long long seed, long long budget_ns, DevInfo* info,
+                                cudaStream_t st);
+cudaError_t launch_os_readout(const double* G, const double* Brot, int m, const double* Vw, int n, double* sig,
+                              int* rank, double* S, double* U, long long ldu, double* V, long long ldv,
+                              cudaStream_t st);
+cudaError_t preload_os_kernels();
 
 // Kernel preloading (one function per source file), for the serving form.
 cudaError_t preload_batched_kernels();

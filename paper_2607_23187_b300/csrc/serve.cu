@@ -191,6 +191,8 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
     if (el == cudaSuccess) el = preload_gemm_kernels();
     if (el == cudaSuccess) el = preload_tc_kernels();
     if (el == cudaSuccess) el = preload_jacobi_kernels();
+    if (el == cudaSuccess) el = preload_svd_kernels();
+    if (el == cudaSuccess) el = preload_os_kernels();
     if (el != cudaSuccess) {
         delete sv;
         return cuda_err(el, "serve: loading the kernels");

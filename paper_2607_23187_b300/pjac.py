@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpjac.so")
 PJAC_OK, PJAC_PENDING = 0, 1
 PJAC_EINVAL, PJAC_ENOMEM, PJAC_EAGAIN = -1, -2, -3
 PJAC_ENOCONV, PJAC_ETIMEOUT, PJAC_ECUDA, PJAC_ENOTIMPL = -4, -5, -6, -7
-PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3}
+PIVOTS = {"gap": 0, "greedy": 1, "cyclic": 2, "random": 3, "gap_rel": 4}
 STOPS = {"offdiag": 0, "libound": 1}
 TRANSFORMS = {"split_bf16": 0, "fp64": 1}
 
@@ -33,7 +33,7 @@ EXPORTS = (
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
     "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
-    "pjac_product_launch_count", "pjac_eig_lowprec",
+    "pjac_product_launch_count", "pjac_eig_lowprec", "pjac_svd", "pjac_svd_onesided", "pjac_probe_fp64",
 )
 
 
@@ -104,6 +104,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                 ctypes.POINTER(Info), vp]
         L.pjac_product.argtypes = [vp, i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]
         L.pjac_eig_lowprec.argtypes = [vp, vp, i, i, vp, i, vp]
+        L.pjac_svd.argtypes = [vp, vp, i, i, i, vp, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
+        L.pjac_svd_onesided.argtypes = [vp, vp, i, i, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
+        L.pjac_probe_fp64.argtypes = [ctypes.POINTER(d), vp]
+        L.pjac_probe_fp64.restype = ctypes.c_int
         L.pjac_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, i, d, vp, vp]
         L.pjac_serve_default_opts.argtypes = [ctypes.POINTER(ServeOpts)]
         L.pjac_serve_default_opts.restype = None
@@ -120,6 +124,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_last_error.argtypes = []
         L.pjac_last_error.restype = ctypes.c_char_p
         for name in ("pjac_create", "pjac_destroy", "pjac_set_opts", "pjac_precondition", "pjac_eig_lowprec",
+                     "pjac_svd", "pjac_svd_onesided",
                      "pjac_solve",
                      "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_create",
                      "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
@@ -272,6 +277,52 @@ def pjac_solve_preconditioned(h: Handle, a1: torch.Tensor, v0: Optional[torch.Te
                                           _ptr(w), _ptr(vt), n, ctypes.byref(info), _stream())
     _check(st, allow)
     return w, vt.t(), info.as_dict(), st
+
+
+def pjac_svd(h: Handle, b: torch.Tensor, pivot: str = "gap", tol: float = 1e-15,
+             vl: Optional[torch.Tensor] = None, vectors: bool = True, allow=(PJAC_OK,)):
+    """One-sided Jacobi SVD of b (m, n), m >= n, FP64 CUDA.  vl: optional
+    (n, n) FP32 right singular vectors (columns).  Returns (S descending,
+    U (m, n), V (n, n), info, status); U and V are None with vectors=False."""
+    if not (b.is_cuda and b.dtype == torch.float64 and b.dim() == 2):
+        raise ValueError("expected an FP64 CUDA matrix")
+    m, n = b.shape
+    bc = b.t().contiguous()                       # column-major storage
+    vlc = None if vl is None else vl.to(device=b.device, dtype=torch.float32).t().contiguous()
+    s = torch.empty(n, dtype=torch.float64, device=b.device)
+    ut = torch.empty((n, m), dtype=torch.float64, device=b.device) if vectors else None
+    vt = torch.empty((n, n), dtype=torch.float64, device=b.device) if vectors else None
+    info = Info()
+    st = load().pjac_svd(h.h, _ptr(bc), m, n, m, _ptr(vlc), n, PIVOTS[pivot], float(tol), _ptr(s), _ptr(ut), m,
+                         _ptr(vt), n, ctypes.byref(info), _stream())
+    _check(st, allow)
+    return s, (None if ut is None else ut.t()), (None if vt is None else vt.t()), info.as_dict(), st
+
+
+def pjac_svd_onesided(h: Handle, b: torch.Tensor, pivot: str = "gap_rel", tol: float = 1e-16,
+                      vectors: bool = True, allow=(PJAC_OK,)):
+    """One-sided Jacobi SVD with inner products recomputed from the columns
+    (relative accuracy, no preconditioner).  b (m, n) FP64 CUDA, m >= n.
+    Returns (S descending, U (m, n), V (n, n), info, status)."""
+    if not (b.is_cuda and b.dtype == torch.float64 and b.dim() == 2):
+        raise ValueError("expected an FP64 CUDA matrix")
+    m, n = b.shape
+    bc = b.t().contiguous()
+    s = torch.empty(n, dtype=torch.float64, device=b.device)
+    ut = torch.empty((n, m), dtype=torch.float64, device=b.device) if vectors else None
+    vt = torch.empty((n, n), dtype=torch.float64, device=b.device) if vectors else None
+    info = Info()
+    st = load().pjac_svd_onesided(h.h, _ptr(bc), m, n, m, PIVOTS[pivot], float(tol), _ptr(s), _ptr(ut), m,
+                                  _ptr(vt), n, ctypes.byref(info), _stream())
+    _check(st, allow)
+    return s, (None if ut is None else ut.t()), (None if vt is None else vt.t()), info.as_dict(), st
+
+
+def probe_fp64_tflops() -> float:
+    """Measured FP64 FMA rate of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(load().pjac_probe_fp64(ctypes.byref(v), _stream()))
+    return v.value
 
 
 def pjac_solve_batched(h: Handle, mats: Sequence[torch.Tensor], pivot: str = "gap", tol: float = 1e-15,

@@ -28,7 +28,7 @@ __all__ = [
     "haar", "exact_sym_product", "sym_from_spectrum", "worked_example",
     "spectrum_clustered", "spectrum_cfg1", "spectrum_cfg2", "spectrum_cfg3",
     "spectrum_p1", "batched_workload", "serving_workload", "Problem",
-    "config_problem",
+    "config_problem", "exact_product", "svd_problem", "SvdProblem", "hilbert_cholesky",
 ]
 
 
@@ -105,6 +105,61 @@ def exact_sym_product(q: np.ndarray, lam: np.ndarray) -> np.ndarray:
     a = hi + lo
     a = np.tril(a) + np.tril(a, -1).T
     return a
+
+
+def exact_product(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """fl(X Y) for rectangular X (m x k) and Y (k x n): the exact product
+    (Ozaki--Ogita--Oishi--Rump slices, summed in double-double with Knuth's
+    TwoSum) rounded once to FP64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    k = x.shape[1]
+    kk = max(1, int(np.ceil(np.log2(max(k, 2)))))
+    bits = (53 - kk) // 2
+    ns = int(np.ceil(53 / bits))
+    xs = _ozaki_slices(x, bits, ns)
+    ys = _ozaki_slices(np.ascontiguousarray(y.T), bits, ns)
+    hi = np.zeros((x.shape[0], y.shape[1]))
+    lo = np.zeros_like(hi)
+    for xa in xs:
+        for yb in ys:
+            hi, e = _two_sum(hi, xa @ yb.T)
+            lo = lo + e
+    return hi + lo
+
+
+@dataclasses.dataclass
+class SvdProblem:
+    b: np.ndarray            # (m, n) FP64
+    sigma: np.ndarray        # the singular values it was built from, descending
+    name: str
+
+
+def svd_problem(m: int, n: int, sigma: np.ndarray, seed: int = 0) -> SvdProblem:
+    """B = fl(U diag(sigma) V^T) with U the first n columns of a Haar (m x m)
+    matrix and V Haar (n x n), the product exact before its one rounding."""
+    rng = np.random.default_rng(seed)
+    u = haar(m, rng)[:, :n]
+    v = haar(n, rng)
+    sig = np.asarray(sigma, dtype=np.float64)
+    uh, ul = _two_prod(u, sig[None, :])
+    b = exact_product(uh, v.T) + ul @ v.T
+    return SvdProblem(b=b, sigma=np.sort(sig)[::-1], name="svd_%dx%d_s%d" % (m, n, seed))
+
+
+def hilbert_cholesky(n: int) -> np.ndarray:
+    """The Cholesky factor C_n of the Hilbert matrix H_n = C_n C_n^T in closed
+    form (Sec. 4.2): c_ij = sqrt(2j-1) ((i-1)!)^2 / ((i+j-1)! (i-j)!) for
+    i >= j (1-based), evaluated in 60-digit arithmetic and rounded once."""
+    import mpmath
+    c = np.zeros((n, n))
+    with mpmath.workdps(60):
+        for i in range(1, n + 1):
+            for j in range(1, i + 1):
+                v = mpmath.sqrt(2 * j - 1) * mpmath.factorial(i - 1) ** 2 / (
+                    mpmath.factorial(i + j - 1) * mpmath.factorial(i - j))
+                c[i - 1, j - 1] = float(v)
+    return c
 
 
 def haar(n: int, rng: np.random.Generator) -> np.ndarray:

@@ -155,10 +155,10 @@ def test_serving_small_first_with_bounded_bypass(pj):
     launches = srv.stats()["launches"]
     srv.close()
     assert order == ["A", "S1", "S2", "S3", "S4", "L", "S5", "S6"]
-    # two single-problem pipelines and six micro-batches of five kernels
+    # two single-problem pipelines and six micro-batches of six kernels
     h = pj.Handle()
     count = pj.load().pjac_solve_launch_count
-    assert launches == count(h.h, 400) + count(h.h, 300) + 6 * 5
+    assert launches == count(h.h, 400) + count(h.h, 300) + 6 * 6
     h.close()
     for name, p in zip(names, probs):
         assert res[name][0] == 0
