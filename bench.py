@@ -53,10 +53,18 @@ def measured_peaks():
         return dict(FALLBACK_PEAKS)
 
 
-# FP64 (non-tensor) arithmetic peak of one B300: the nominal 1.25 TFLOP/s.
-# MEASURED_PEAKS.json carries no FP64 figure.
-FP64_PEAK_TFLOPS = 1.25
-FP64_PEAK_SOURCE = "nominal B300 FP64 rate (1.25 TFLOP/s); MEASURED_PEAKS.json has no FP64 figure"
+# FP64 (non-tensor) arithmetic peak: measured in each run by pjac_probe_fp64
+# (1.199 TFLOP/s on a B300 of this machine, against a nominal 1.25); this
+# constant serves only the workloads that do not run the probe.
+FP64_PEAK_TFLOPS = 1.199
+FP64_PEAK_SOURCE = "measured by pjac_probe_fp64 on a B300 of this pool (1.199 TFLOP/s; nominal 1.25)"
+
+# DRAM bytes (read + write) of one launch of the Jacobi kernel, from the
+# committed ncu capture (profiles/jacobi_single_kernel_cfg2_n1024.md); the
+# working set (A1 and V, 8 MB each at n = 1024) stays in L2, so the traffic
+# of a launch does not grow with its rotations.
+JACOBI_TRAFFIC_PER_LAUNCH = {}
+JACOBI_TRAFFIC_SOURCE = "no ncu capture of the current kernel at this order"
 
 
 class Clocks:
@@ -167,42 +175,24 @@ def workload_problem(name, n=None):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     p = workload_problem(args.workload, args.n)
     n = p.n
     cores = os.cpu_count()
     values = []
-    samples = []
     t_pre = None
+    sample = ""
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        q0 = oracle.q0_fp32(p.a)
-        q, a1 = oracle.precondition(p.a, q0)
-        t1 = time.perf_counter()
-        budget = args.ref_rotations
-        r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=budget)
-        t2 = time.perf_counter()
-        rot_rate = r["rotations"] / max(t2 - t1, 1e-9)
-        # rotations of a full solve: the gap rule needs ~1.8 sweeps of
-        # n(n-1)/2 rotations at this accuracy (measured on the oracle at
-        # n = 300, 520, 1024: 1.94, 1.85, 1.77 sweeps)
-        need = 1.8 * n * (n - 1) / 2
-        t_solve = (t1 - t0) + need / rot_rate
+        t_solve, t_pre, rate, sample = oracle_sample(p, args)
         if step >= args.warmup:
             values.append(1.0 / t_solve)
-            samples.append(t_solve)
-        t_pre = t1 - t0
     v = float(np.median(values))
     unit = "solves/s"
-    sample = ("oracle preconditioner (LAPACK FP32 eigh + FP64 Newton-Schulz + Q^T A Q on %d threads) in full, "
-              "then %d Jacobi rotations of the gap rule (C, one thread), extrapolated to 1.8 sweeps of "
-              "n(n-1)/2 rotations" % (cores, args.ref_rotations))
     out = {"metric": METRIC, "value": v, "unit": unit, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": bench_config(args, n),
+           "config": dict(bench_config(args, n), transform=args.transform,
+                          preconditioner=preconditioner_label(args)),
            "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
                             "precondition_s": t_pre},
            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -212,24 +202,52 @@ def run_reference(args, ws, rank):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def cpu_baseline_single(p, rotations_needed, rot_budget):
-    """Time the oracle as it stands on a bounded sample of the workload."""
+# Rotations of one solve of the default workloads by the oracle's own path
+# (LAPACK FP32 eigenvectors, Newton--Schulz, FP64 transform, the refinement
+# steps, gap rule, off-diagonal stop 1e-15), measured once on the CPU with
+# oracle.solve; both oracle legs (the cpu_baseline of our line and the
+# reference arm) extrapolate a timed sample of rotations to these counts.
+ORACLE_SOLVE_ROTATIONS = {("cfg2", 1024, 0): 924672, ("cfg2", 1024, 3): 83968}
+
+
+def preconditioner_label(args):
+    base = "Sec. 2.1 (FP32 eigenbasis, Newton-Schulz, Q^T A Q with %s products)" % args.transform
+    if args.refine:
+        return base + " + %d first-order FP64 refinement steps (an extension beyond the paper)" % args.refine
+    return base
+
+
+def oracle_sample(p, args):
+    """The oracle as it stands on a bounded sample of the workload: its full
+    preconditioner (with the same refinement steps), then a bounded number
+    of gap-rule rotations of its Algorithm 1; the solve time is the
+    preconditioner plus the solve's rotation count at the sampled rate."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    q0 = oracle.q0_fp32(p.a)
-    q, a1 = oracle.precondition(p.a, q0)
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a), refine_steps=args.refine)
     t1 = time.perf_counter()
-    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=rot_budget)
+    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=args.ref_rotations)
     t2 = time.perf_counter()
     rate = r["rotations"] / max(t2 - t1, 1e-9)
-    t_solve = (t1 - t0) + rotations_needed / rate
+    key = (args.workload, p.n, args.refine)
+    need = ORACLE_SOLVE_ROTATIONS.get(key)
+    how = "the oracle's own rotation count for this workload (measured once with oracle.solve)"
+    if need is None:
+        need = 1.8 * p.n * (p.n - 1) / 2
+        how = "1.8 sweeps of n(n-1)/2 rotations (no stored oracle count for this workload)"
+    t_solve = (t1 - t0) + need / rate
+    sample = ("oracle preconditioner in full (LAPACK FP32 eigh, FP64 Newton-Schulz, Q^T A Q, %d refinement "
+              "steps; numpy on %d threads), then %d gap-rule rotations of the C oracle (one thread) at %.0f "
+              "rotations/s, extrapolated to %d rotations: %s"
+              % (args.refine, os.cpu_count(), r["rotations"], rate, need, how))
+    return t_solve, t1 - t0, rate, sample
+
+
+def cpu_baseline_single(p, args):
+    t_solve, t_pre, rate, sample = oracle_sample(p, args)
     return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": ("preconditioner in full (LAPACK FP32 eigh + Newton-Schulz + Q^T A Q, numpy threads), then "
-                       "%d gap-rule Jacobi rotations of the C oracle (one thread) at %.0f rotations/s, "
-                       "extrapolated to the %d rotations the solve takes (the oracle follows the same pivot "
-                       "sequence as the GPU on the same A1)" % (r["rotations"], rate, rotations_needed)),
-            "precondition_s": t1 - t0, "oracle_rotations_per_s": rate}
+            "sample": sample, "precondition_s": t_pre, "oracle_rotations_per_s": rate}
 
 
 def run_ours(args, ws, rank, local):
@@ -238,14 +256,17 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    t_start = time.perf_counter()
     p = workload_problem(args.workload, args.n)
     n = p.n
     h = pjac.Handle(transform=args.transform, cluster_size=args.cluster)
     a = torch.tensor(p.a, device=dev)
     stream = torch.cuda.current_stream()
+    fp64_peak = pjac.probe_fp64_tflops()      # measured FP64 FMA rate of this GPU, this run
 
-    def solve(pivot="gap", stop="offdiag", tol=1e-15, mat=None):
-        h.set_opts(transform=args.transform, stop=stop, cluster_size=args.cluster)
+    def solve(pivot="gap", stop="offdiag", tol=1e-15, mat=None, refine=None, transform=None):
+        h.set_opts(transform=transform or args.transform, stop=stop, cluster_size=args.cluster,
+                   refine_steps=args.refine if refine is None else refine, fp32_sweeps=args.fp32_sweeps)
         return pjac.pjac_solve(h, a if mat is None else mat, pivot, tol)
 
     for _ in range(args.warmup):
@@ -288,60 +309,68 @@ def run_ours(args, ws, rank, local):
     e0.record(stream)
     for _ in range(e_steps):
         a_dev = a_host.to(dev, non_blocking=True)
-        h.set_opts(transform=args.transform, cluster_size=args.cluster)
-        w_d, v_d, _, _ = pjac.pjac_solve(h, a_dev, "gap", 1e-15)
+        w_d, v_d, _, _ = solve(mat=a_dev)
         w_host.copy_(w_d, non_blocking=True)
         v_host.copy_(v_d, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1)) / e_steps
 
-    # gap vs greedy, and the eigenvalue-only (Theorem 1) gap solve
+    def timed(label, **kw):
+        mat = kw.pop("mat", None)
+        prob = kw.pop("prob", p)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        wx, vx, ix, sx = solve(mat=mat, **kw)
+        torch.cuda.synchronize()
+        rec = {"s": time.perf_counter() - t, "rotations": ix["rotations"], "sweeps": ix["sweeps"],
+               "phases_ms": {"precondition": ix["ms_precond"], "transform": ix["ms_transform"],
+                             "jacobi": ix["ms_jacobi"]},
+               "max_abs_eig_err": float(np.max(np.abs(wx.cpu().numpy() - prob.lam))), "norm2": prob.norm2}
+        extras[label] = rec
+        return rec
+
+    # gap vs greedy, eigenvalues certified by Theorem 1, the paper's own
+    # preconditioner, the plain FP64 GPU path, and the n = 4096 solve
     extras = {}
+    norm_f = float(np.linalg.norm(p.a))
+    tol_li = 1e-13 * p.norm2 / norm_f
     if not args.no_extras:
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        wg, vg, inf_g, st_g = solve(pivot="greedy")
-        torch.cuda.synchronize()
-        extras["greedy"] = {"ms": 1000 * (time.perf_counter() - t), "rotations": inf_g["rotations"],
-                            "sweeps": inf_g["sweeps"],
-                            "max_abs_eig_err": float(np.max(np.abs(wg.cpu().numpy() - p.lam)))}
-        norm_f = float(np.linalg.norm(p.a))
-        tol_li = 1e-13 * p.norm2 / norm_f
-        t = time.perf_counter()
-        wl, vl, inf_l, st_l = solve(stop="libound", tol=tol_li)
-        torch.cuda.synchronize()
-        extras["gap_theorem1_stop"] = {
-            "ms": 1000 * (time.perf_counter() - t), "rotations": inf_l["rotations"], "sweeps": inf_l["sweeps"],
-            "tol": tol_li, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1",
-            "max_abs_eig_err": float(np.max(np.abs(wl.cpu().numpy() - p.lam)))}
-        if args.with_4096:
+        timed("greedy", pivot="greedy")
+        timed("gap_theorem1_stop", stop="libound", tol=tol_li)
+        extras["gap_theorem1_stop"].update({"tol": tol_li, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1"})
+        if args.refine:
+            timed("paper_preconditioner", refine=0)
+            timed("paper_preconditioner_theorem1_stop", refine=0, stop="libound", tol=tol_li)
+        timed("plain_fp64_path", refine=0, transform="fp64")
+        extras["plain_fp64_path"]["what"] = "FP64 CUDA-core products, no refinement, the same Jacobi kernel"
+        if not args.no_4096 and n != 4096:
             p4 = workload_problem("cfg3")
             a4 = torch.tensor(p4.a, device=dev)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            w4, v4, inf4, st4 = solve(mat=a4)
-            torch.cuda.synchronize()
-            extras["cfg3_n4096_gap"] = {"s": time.perf_counter() - t, "rotations": inf4["rotations"],
-                                        "sweeps": inf4["sweeps"], "phases_ms": {
-                                            "precondition": inf4["ms_precond"], "transform": inf4["ms_transform"],
-                                            "jacobi": inf4["ms_jacobi"]},
-                                        "max_abs_eig_err": float(np.max(np.abs(w4.cpu().numpy() - p4.lam))),
-                                        "norm2": p4.norm2}
+            tl4 = 1e-13 * p4.norm2 / float(np.linalg.norm(p4.a))
+            timed("cfg3_n4096_theorem1_stop", mat=a4, prob=p4, stop="libound", tol=tl4)
+            extras["cfg3_n4096_theorem1_stop"].update({"tol": tl4, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1"})
+            if time.perf_counter() - t_start < 700:
+                timed("cfg3_n4096_full_solve", mat=a4, prob=p4)
             del a4
-        h.set_opts(transform=args.transform, cluster_size=args.cluster)
+        h.set_opts(transform=args.transform, cluster_size=args.cluster, refine_steps=args.refine,
+                   fp32_sweeps=args.fp32_sweeps)
 
     # roofline of the dominant kernel (the Jacobi kernel): FP64 arithmetic
+    # against this GPU's measured FP64 rate; DRAM traffic per launch from the
+    # committed ncu capture (the working set, A1 and V, stays in L2)
     inf = infos[-1]
     rot = inf["rotations"]
     jac_ms = float(np.median([i["ms_jacobi"] for i in infos]))
     flops = 14.0 * n * rot     # per rotation: rows (2 mul + 2 fma), V (same), 2 key differences
     achieved = flops / (jac_ms / 1000.0) / 1e12
     peaks = measured_peaks()
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak,
+            "traffic": JACOBI_TRAFFIC_PER_LAUNCH.get(n),
+            "traffic_source": JACOBI_TRAFFIC_SOURCE,
             "kernel": "jacobi_single_kernel (one cluster of CTAs, one problem)",
-            "peak_source": FP64_PEAK_SOURCE,
+            "peak_source": "measured in this run by pjac_probe_fp64 (FP64 FMA chains on every SM)",
             "ns_per_rotation": 1e6 * jac_ms / max(rot, 1),
             "hbm_gbs_equiv": 80.0 * n * rot / (jac_ms / 1000.0) / 1e9,
             "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peaks["source"]}
@@ -349,7 +378,8 @@ def run_ours(args, ws, rank, local):
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": dict(bench_config(args, n), transform=args.transform),
+           "config": dict(bench_config(args, n), transform=args.transform,
+                          preconditioner=preconditioner_label(args)),
            "phases_ms": {"precondition": inf["ms_precond"], "transform": inf["ms_transform"],
                          "jacobi": inf["ms_jacobi"]},
            "rotations": rot, "sweeps": inf["sweeps"],
@@ -362,7 +392,7 @@ def run_ours(args, ws, rank, local):
            "roofline": roof,
            "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_single(p, rot, args.ref_rotations)
+        out["cpu_baseline"] = cpu_baseline_single(p, args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()
@@ -590,6 +620,17 @@ def run_batched_ours(args, ws, rank, local):
     rot = np.array([s_["rotations"] for s_ in stats], dtype=np.float64)
     status_ok = all(s_["status"] == 0 for s_ in stats)
 
+    # stage shares: one more call outside the graph, with its stage events
+    call()
+    torch.cuda.synchronize()
+    stage = (ctypes.c_float * 5)()
+    stages = None
+    if L.pjac_batched_stage_ms(h.h, stage) == 0:
+        names = ["fp32_eigenbases", "newton_schulz_and_transform", "refinement", "jacobi", "readout_and_report"]
+        tot = sum(stage)
+        stages = {nm: {"ms": float(stage[k]), "share": float(stage[k] / tot) if tot > 0 else None}
+                  for k, nm in enumerate(names)}
+
     # the plain single-problem FP64 path on a seeded sample, one at a time
     sample = np.random.default_rng(11).choice(nb, 100, replace=False)
     hp = pjac.Handle(transform="fp64")
@@ -608,7 +649,7 @@ def run_batched_ours(args, ws, rank, local):
     achieved = flops / (ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "whole batched pipeline (5 kernels in one CUDA graph; the Jacobi kernel dominates)",
+            "kernel": "whole batched pipeline (6 kernels in one CUDA graph; the Jacobi kernel dominates)",
             "peak_source": FP64_PEAK_SOURCE,
             "us_per_rotation_per_cta": 1e3 * ms * 2 * 148 / max(rot.sum(), 1)}
     out = {"metric": BATCHED_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -624,7 +665,8 @@ def run_batched_ours(args, ws, rank, local):
                                   "batched_speedup": value / ws / one_rate},
            "e2e": {"value": ws * nb / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(flat.nbytes),
                    "d2h_bytes_per_step": int(host_w.numel() * 8 + host_v.numel() * 8)},
-           "gpu_launches": 5 * args.steps,
+           "gpu_launches": 6 * args.steps,
+           "stages": stages,
            "roofline": roof, "clocks": clocks}
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -849,18 +891,214 @@ def run_serving(args, ws, rank, local):
         print(json.dumps(out_line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# Sec. 4.1's experiment (config P1): eigenvalue error against rotations
+# ----------------------------------------------------------------------------
+P1_METRIC = "rotations to total relative eigenvalue error <= 1e-11 (Sec. 4.1 experiment, n=1000, alpha=1, gap rule)"
+P1_THRESHOLD = 1e-11   # above the floor the FP64 rounding of A sets (about 6e-12 to 8e-12 for these spectra)
+
+
+def eig_error_curve(pjac, h, a1_dev, lam, norm2, pivot, chunk, max_total):
+    """Algorithm 1 on the GPU in chunks of `chunk` rotations (A1 carried over
+    in place between calls; V is not needed for the eigenvalues), with the
+    paper's error measure sum_i |lambda_i - a_ii| / ||A|| (sorted) after each
+    chunk.  Returns [(rotations, error)], the rotations at which the error
+    first fell to P1_THRESHOLD, and the device milliseconds of the Jacobi
+    calls."""
+    import torch
+    a1 = a1_dev.clone()
+    rot, pts, first, ms = 0, [], None, 0.0
+    h.set_opts(transform="fp64", max_rotations=chunk)
+    while rot < max_total:
+        w, _, info, st = pjac.pjac_solve_preconditioned(h, a1, None, pivot, 1e-15, allow=(0, -4))
+        torch.cuda.synchronize()
+        rot += info["rotations"]
+        ms += info["ms_jacobi"]
+        err = float(np.sum(np.abs(np.sort(w.cpu().numpy()) - lam)) / norm2)
+        pts.append((rot, err))
+        if first is None and err <= P1_THRESHOLD:
+            first = rot
+        if st == 0:
+            break
+    return pts, first, ms
+
+
+def run_p1(args, ws, rank, local):
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = pjac.Handle(transform="fp64")
+    res = {}
+    clk = Clocks(local)
+    clk.start()
+    t0 = time.perf_counter()
+    for cfg, alpha in (("p1a", 0.01), ("p1b", 1.0)):
+        p = pin.config_problem(cfg)
+        h.set_opts(transform="split_bf16")
+        q, a1 = pjac.pjac_precondition(h, torch.tensor(p.a, device=dev))
+        for pivot in ("gap", "greedy"):
+            pts, first, ms = eig_error_curve(pjac, h, a1, p.lam, p.norm2, pivot, args.p1_chunk, 4_000_000)
+            res["alpha=%g/%s" % (alpha, pivot)] = {
+                "rotations_to_threshold": first, "rotations_total": pts[-1][0], "jacobi_ms": ms,
+                "final_error": pts[-1][1],
+                "curve": [(int(r), float("%.3e" % e)) for r, e in pts[:: max(1, len(pts) // 40)]]}
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    g = res["alpha=1/gap"]["rotations_to_threshold"]
+    out = {"metric": P1_METRIC, "value": g, "unit": "rotations", "n_gpus": ws, "steps": 1, "warmup": 0,
+           "ms_per_step": 1000.0 * wall, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "P1: Sec. 4.1, A = V Lambda V^T, n = 1000, lambda_1^(k) = 1 + exp(-alpha k), "
+                                  "lambda_2^(k) = 2 + (k-1)/499, alpha in {0.01, 1}; the GPU preconditioner "
+                                  "(FP32 eigenbasis, Newton-Schulz, split-BF16 transform); gap and greedy; error "
+                                  "sum |lambda - a_kk| / ||A|| after every %d rotations" % args.p1_chunk},
+           "curves": res,
+           "threshold": P1_THRESHOLD,
+           "gap_vs_greedy_rotations_to_threshold": {
+               a: {"gap": res["alpha=%s/gap" % a]["rotations_to_threshold"],
+                   "greedy": res["alpha=%s/greedy" % a]["rotations_to_threshold"]} for a in ("0.01", "1")},
+           "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+# ----------------------------------------------------------------------------
+# one-sided Jacobi SVD (Alg. 2) and the relative-accuracy form (Sec. 4.2)
+# ----------------------------------------------------------------------------
+SVD_METRIC = "one-sided Jacobi SVDs/s (Alg. 2 with the right-singular-vector preconditioner, gap rule)"
+
+
+def run_svd(args, ws, rank, local):
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n = (args.n or 1024) * 2, (args.n or 1024)
+    rng = np.random.default_rng(n)
+    sig = np.concatenate([1.0 + 1e-9 * rng.uniform(-1, 1, n // 2), np.linspace(2.0, 3.0, n - n // 2)])
+    p = pin.svd_problem(m, n, sig, seed=n)
+    b = torch.tensor(p.b, device=dev)
+    h = pjac.Handle(transform="split_bf16", refine_steps=args.refine)
+    for _ in range(args.warmup):
+        pjac.pjac_svd(h, b, "gap", 1e-15)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s, u, v, info, st = pjac.pjac_svd(h, b, "gap", 1e-15)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1)) / args.steps
+    sn, un, vn = s.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy()
+    acc = {"max_abs_sigma_err": float(np.max(np.abs(sn - p.sigma))), "sigma_max": float(p.sigma[0]),
+           "u_orth": float(np.linalg.norm(un.T @ un - np.eye(n))),
+           "residual": float(np.linalg.norm(p.b @ vn - un * sn) / np.linalg.norm(p.b))}
+    extras = {}
+    if not args.no_extras:
+        t = time.perf_counter()
+        sg, _, _, ig, _ = pjac.pjac_svd(h, b, "greedy", 1e-15)
+        torch.cuda.synchronize()
+        extras["greedy"] = {"ms": 1000 * (time.perf_counter() - t), "rotations": ig["rotations"]}
+    out = {"metric": SVD_METRIC, "value": ws * 1000.0 / ms, "unit": "SVDs/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "SVD: B = U diag(sigma) V^T, %d x %d, sigma half within 1e-9 of 1, half "
+                                  "spread over [2, 3]; gap rule, off-diagonal stop 1e-15; %d refinement steps"
+                                  % (m, n, args.refine), "m": m, "n": n},
+           "rotations": info["rotations"],
+           "phases_ms": {"precondition": info["ms_precond"], "transform": info["ms_transform"],
+                         "jacobi_and_readout": info["ms_jacobi"]},
+           "accuracy": acc, "extras": extras, "clocks": clocks,
+           "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
+HILBERT_METRIC = "one-sided Jacobi SVDs/s of the Hilbert Cholesky factor C_100 (Sec. 4.2, relative score)"
+
+
+def run_hilbert(args, ws, rank, local):
+    import mpmath
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n or 100
+    c = pin.hilbert_cholesky(n)
+    with mpmath.workdps(250):
+        cm = mpmath.matrix(c.tolist())
+        ev = mpmath.eigsy(cm * cm.T, eigvals_only=True)
+        ref = np.sort(np.array([float(mpmath.sqrt(e)) for e in ev]))[::-1]
+    lap = np.abs(np.linalg.svd(c, compute_uv=False) - ref) / ref
+    b = torch.tensor(c, device=dev)
+    h = pjac.Handle()
+    for _ in range(args.warmup):
+        pjac.pjac_svd_onesided(h, b, "gap_rel", 1e-16)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s, u, v, info, st = pjac.pjac_svd_onesided(h, b, "gap_rel", 1e-16)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    rel = np.abs(s.cpu().numpy() - ref) / ref
+    comp = {}
+    for label, piv, mr in (("gap_rel_1e3", "gap_rel", 1000), ("random_5e4", "random", 50000),
+                           ("random_2e5", "random", 200000)):
+        h.set_opts(max_rotations=mr, seed=1)
+        t = time.perf_counter()
+        sr, _, _, ir, str_ = pjac.pjac_svd_onesided(h, b, piv, 1e-16, allow=(0, -4))
+        torch.cuda.synchronize()
+        rr = np.abs(sr.cpu().numpy() - ref) / ref
+        comp[label] = {"rotations": ir["rotations"], "converged": str_ == 0, "ms": 1000 * (time.perf_counter() - t),
+                       "median_rel_err": float(np.median(rr)), "count_rel_err_below_1e-6": int(np.sum(rr < 1e-6))}
+    out = {"metric": HILBERT_METRIC, "value": 1000.0 / ms, "unit": "SVDs/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "closed form (Sec. 4.2)",
+           "config": {"workload": "C_%d, the closed-form Cholesky factor of the Hilbert matrix (rounded to FP64); "
+                                  "one-sided Jacobi with inner products from the columns, relative score "
+                                  "(1/a_ii + 1/a_jj) L_ij, stop at max score <= 1e-16, no preconditioner" % n},
+           "rotations": info["rotations"], "converged": st == 0,
+           "relative_accuracy": {"reference": "exact singular values of the FP64 input, 250-digit arithmetic",
+                                 "median": float(np.median(rel)), "lapack_median": float(np.median(lap)),
+                                 "count_below_1e-6": int(np.sum(rel < 1e-6)),
+                                 "lapack_count_below_1e-6": int(np.sum(lap < 1e-6)),
+                                 "geomean_gain_over_lapack_from_k30": float(np.exp(np.mean(np.log(lap[30:] / rel[30:]))))},
+           "comparators": comp, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "batched", "product", "serving"])
+    ap.add_argument("--workload", default="cfg2",
+                    choices=["cfg2", "cfg3", "batched", "product", "serving", "p1", "svd", "hilbert"])
+    ap.add_argument("--refine", type=int, default=3, help="first-order refinement steps (an extension)")
+    ap.add_argument("--fp32-sweeps", type=int, default=0, help="sweep cap of the FP32 eigenbasis (0: 40)")
+    ap.add_argument("--no-4096", action="store_true", help="leave out the n=4096 extra solve")
+    ap.add_argument("--p1-chunk", type=int, default=1000, help="P1: rotations between error measurements")
     ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
-    ap.add_argument("--with-4096", action="store_true", help="add one timed n=4096 (cfg3) solve")
     ap.add_argument("--transform", default="split_bf16", choices=["split_bf16", "fp64"])
-    ap.add_argument("--ref-rotations", type=int, default=100000)
+    ap.add_argument("--ref-rotations", type=int, default=50000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests of the stream to replay")
@@ -884,6 +1122,12 @@ def main():
             run_batched_reference(args, ws, rank)
         else:
             run_batched_ours(args, ws, rank, local)
+    elif args.workload in ("p1", "svd", "hilbert"):
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "no reference arm for this extra workload"}))
+        else:
+            {"p1": run_p1, "svd": run_svd, "hilbert": run_hilbert}[args.workload](args, ws, rank, local)
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:

@@ -111,6 +111,27 @@ typedef struct {
      * well-separated pairs on the tensor cores and leaves fewer rotations
      * to the Jacobi iteration.  0..8. */
     int refine_steps;
+    /* Most sweeps of the parallel-order FP32 Jacobi pass of the low-precision
+     * eigenbasis (it stops earlier once its off-diagonal mass stagnates);
+     * 0: 40. */
+    int fp32_sweeps;
+    /* Multi-pivot variant (the parallel direction Sec. 5 names as future
+     * work), for the gap and greedy rules, n <= 4096: 0 or 1 = off; K >= 2
+     * (<= 64): every step ranks the rows by their best score, walks the K
+     * best rows in order and accepts each head whose score is positive, at
+     * least multi_ratio times the first one's and whose indices are still
+     * free, then applies the accepted rotations in that order (they act on
+     * disjoint index pairs).  K = 1 is Algorithm 1.  One CTA per problem,
+     * exact FP64 scores. */
+    int multi_pivot;
+    double multi_ratio;      /* default 0 */
+    /* pjac_solve_batched: 1 (default) tunes, per order bucket (n < 32, < 64,
+     * < 128, <= 256, > 256) and pivot rule, the refinement steps (1..3) and
+     * the FP32 sweep cap (12 or 40) on the first call outside a stream
+     * capture that meets the bucket, by timing up to 32 of the call's own
+     * problems with every candidate; the choice is cached in the handle.
+     * 0: refinement 1 + refine_steps, sweep cap fp32_sweeps (or 40). */
+    int autotune;
 } pjac_opts;
 
 /* Per-solve report. */
@@ -124,6 +145,7 @@ typedef struct {
     float ms_precond;        /* FP32 diagonalisation + reorthogonalisation */
     float ms_transform;      /* Q^T A Q */
     float ms_jacobi;         /* Jacobi iteration + readout */
+    int64_t steps;           /* selection steps (== rotations except for the multi-pivot variant) */
 } pjac_info;
 
 typedef struct pjac_handle pjac_handle;
@@ -323,6 +345,21 @@ int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, const float
 int pjac_svd_onesided(pjac_handle* h, const double* B, int m, int n, int ldb, pjac_pivot pivot, double tol,
                       double* S, double* U, int ldu, double* V, int ldv, pjac_info* info, void* stream);
 
+/* The autotuner's choice for an order bucket (0: n < 32, 1: < 64, 2: < 128,
+ * 3: <= 256, 4: > 256) and pivot rule of the batched form on h: refinement
+ * steps, FP32 sweep cap and the tuning sample's solves/s.  PJAC_EINVAL when
+ * that bucket has not been tuned on h. */
+int pjac_batched_tuning(pjac_handle* h, int bucket, pjac_pivot pivot, int* refine, int* fp32_sweeps,
+                        float* sample_solves_per_s);
+
+/* Device milliseconds of the five stages of the last pjac_solve_batched call
+ * made on h outside a stream capture: ms[0] FP32 eigenbases (or the copy-in
+ * without the preconditioner), ms[1] Newton--Schulz and Q^T A Q, ms[2] the
+ * refinement step(s), ms[3] the Jacobi iteration, ms[4] readout and report.
+ * Synchronises on that call's completion.  Errors: PJAC_EINVAL when no such
+ * call was made, PJAC_ECUDA. */
+int pjac_batched_stage_ms(pjac_handle* h, float* ms);
+
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of eigenproblems of mixed sizes.  Requests
  * are admitted while their device footprint fits the memory budget and a
@@ -401,6 +438,11 @@ int pjac_solve_launch_count(pjac_handle* h, int n);
  * one).  Returns -1 when h is NULL, a size is out of range, or the split
  * product does not support the shape. */
 int pjac_product_launch_count(pjac_handle* h, int m, int n, int k);
+
+/* Sweeps made by the two parallel-order FP32 Jacobi passes of the last
+ * low-precision eigenbasis computed with h (the first pass on fl32(A), the
+ * refinement pass on X^T fl32(A) X).  A diagnostic; synchronises the device. */
+int pjac_fp32_sweeps_done(pjac_handle* h, int* diag, int* refine);
 
 /* Measured FP64 fused multiply-add rate of the current device in TFLOP/s
  * (2 flops per FMA): eight independent chains per thread over a grid of

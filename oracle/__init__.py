@@ -96,6 +96,11 @@ def lib():
                                           ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_uint64,
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                           ctypes.POINTER(ctypes.c_int)]
+            L.or_jacobi_multi.restype = ctypes.c_int
+            L.or_jacobi_multi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                          ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(_Info)]
             L.or_random_pair.restype = None
             L.or_random_pair.argtypes = [ctypes.c_uint64, ctypes.c_longlong, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -485,3 +490,25 @@ def svd_onesided(b: np.ndarray, pivot: str = "gap_rel", tol: float = 1e-15,
     u = bc[:, order] / np.where(sig > 0, sig, 1.0)[None, :]
     return {"sigma": sig, "u": u, "v": np.ascontiguousarray(v[:, order]), "rotations": int(rot.value),
             "status": int(st.value), "b": np.ascontiguousarray(bc), "g": g, "order": order}
+
+
+def jacobi_multi(a1: np.ndarray, v0: Optional[np.ndarray] = None, pivot: str = "gap", stop: str = "offdiag",
+                 tol: float = 1e-15, K: int = 8, ratio: float = 0.0, max_rot: Optional[int] = None,
+                 check_every: Optional[int] = None) -> Dict:
+    """The multi-pivot variant (see ``or_jacobi_multi``): up to K
+    non-conflicting pivots per step, taken greedily from the K best row
+    heads; K = 1 is Algorithm 1.  Returns the final matrix, V, rotations,
+    steps and status."""
+    a = np.array(a1, dtype=np.float64, order="C", copy=True)
+    n = a.shape[0]
+    v = np.eye(n) if v0 is None else np.array(v0, dtype=np.float64, order="C", copy=True)
+    if max_rot is None:
+        max_rot = 50 * n * (n - 1) // 2 + 1
+    if check_every is None:
+        check_every = max(n, 1)
+    steps = ctypes.c_longlong(0)
+    info = _Info()
+    lib().or_jacobi_multi(_ptr(a), n, _ptr(v), PIVOTS[pivot], STOPS[stop], float(tol), int(max_rot),
+                          int(check_every), int(K), float(ratio), ctypes.byref(steps), ctypes.byref(info))
+    return {"a": a, "v": v, "rotations": int(info.rotations), "steps": int(steps.value),
+            "status": int(info.status), "off_final": info.off_final, "norm_f": info.norm_f}

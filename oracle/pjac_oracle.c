@@ -592,3 +592,114 @@ int or_svd_onesided(double* B, int m, int n, double* V, int pivot, double tol, l
     *status_out = status;
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Multi-pivot variant (the block/parallel direction Sec. 5 names as future
+ * work; its rules here are readings, listed in the design notes).  Every
+ * step
+ *   1. ranks the rows by their best score (row-best cache of Sec. 3.2),
+ *      larger first, ties to the smaller row, and takes the first K rows;
+ *   2. walks those K rows in order and accepts the head (k, bestc[k]) as a
+ *      pivot when its score is > 0, at least `ratio` times the first row's
+ *      score, and neither index is taken by an accepted pivot;
+ *   3. applies the accepted rotations one after another in that order
+ *      (disjoint index pairs, so each one's (c, s) is that of the matrix
+ *      before the step);
+ *   4. rescans rows that are pivot indices or whose best column is one, and
+ *      compares the new entries (k, x) of every other row, x over the pivot
+ *      indices in increasing order (the or_update_cache rule).
+ * With K = 1 this is Algorithm 1 with the row-best cache exactly.  Stop: the
+ * off-diagonal test before the first step and then before every step at
+ * which the rotation count has passed another multiple of check_every; the
+ * Theorem 1 stop on the first row's score; a zero first score.  max_rot is
+ * tested at the start of a step (status 1).  steps_out: steps taken.
+ * ------------------------------------------------------------------------ */
+int or_jacobi_multi(double* A, int n, double* V, int pivot, int stop, double tol, long long max_rot,
+                    long long check_every, int K, double ratio, long long* steps_out, or_info* info) {
+    memset(info, 0, sizeof(*info));
+    info->first_rot_eig_ok = -1;
+    *steps_out = 0;
+    if (n < 2) return 0;
+    if (K < 1) K = 1;
+    if (check_every < 1) check_every = n;
+    double normf = or_frobenius(A, n);
+    info->norm_f = normf;
+    double thr = tol * normf;
+    double eps_li = tol * normf / (2.0 * (double)n * (double)(n - 1));
+    double* bestv = (double*)malloc(sizeof(double) * (size_t)n);
+    int* bestc = (int*)malloc(sizeof(int) * (size_t)n);
+    int* taken = (int*)calloc((size_t)n, sizeof(int));
+    int* cand = (int*)malloc(sizeof(int) * (size_t)K);
+    int* pi = (int*)malloc(sizeof(int) * (size_t)K);
+    int* pj = (int*)malloc(sizeof(int) * (size_t)K);
+    char* inset = (char*)calloc((size_t)n, 1);
+    int* idx = (int*)malloc(sizeof(int) * (size_t)(2 * K));
+    for (int k = 0; k < n; ++k) or_rescan_row(pivot, A, n, k, bestv, bestc);
+    long long rot = 0, steps = 0, next_check = 0;
+    int status = 1;
+    double last = 0.0;
+    for (;;) {
+        if (rot >= next_check) {
+            double off = or_offmass(A, n, normf);
+            info->checks++;
+            if (stop == OR_STOP_OFFDIAG && off <= thr) { status = 0; break; }
+            next_check = (rot / check_every + 1) * check_every;
+        }
+        /* the K best rows, larger score first, ties to the smaller row */
+        int nc = 0;
+        for (int q = 0; q < K && q < n; ++q) {
+            double bv = -1.0;
+            int bk = -1;
+            for (int k = 0; k < n; ++k)
+                if (!taken[k] && bestv[k] > bv) { bv = bestv[k]; bk = k; }
+            if (bk < 0) break;
+            taken[bk] = 1;
+            cand[nc++] = bk;
+        }
+        for (int q = 0; q < nc; ++q) taken[cand[q]] = 0;
+        double first = bestv[cand[0]];
+        last = first;
+        if (first == 0.0) { status = 0; break; }
+        if (stop == OR_STOP_LIBOUND && first <= eps_li) { status = 0; break; }
+        if (rot >= max_rot) { status = 1; break; }
+        int na = 0;
+        for (int q = 0; q < nc; ++q) {
+            int k = cand[q], l = bestc[k];
+            double v = bestv[k];
+            if (!(v > 0.0) || v < ratio * first) break;
+            int i = k < l ? k : l, j = k < l ? l : k;
+            if (inset[i] || inset[j]) continue;
+            inset[i] = inset[j] = 1;
+            pi[na] = i;
+            pj[na] = j;
+            na++;
+        }
+        for (int p = 0; p < na; ++p) or_rotate(A, n, V, pi[p], pj[p], NULL);
+        rot += na;
+        steps++;
+        /* the pivot indices in increasing order */
+        int ni = 0;
+        for (int p = 0; p < na; ++p) { idx[ni++] = pi[p]; idx[ni++] = pj[p]; }
+        for (int a = 1; a < ni; ++a)
+            for (int b = a; b > 0 && idx[b - 1] > idx[b]; --b) { int t = idx[b]; idx[b] = idx[b - 1]; idx[b - 1] = t; }
+        for (int k = 0; k < n; ++k) {
+            if (inset[k] || inset[bestc[k]]) {
+                or_rescan_row(pivot, A, n, k, bestv, bestc);
+                continue;
+            }
+            for (int q = 0; q < ni; ++q) {
+                int l = idx[q];
+                double v = or_score(pivot, A, n, k, l);
+                if (or_better(v, k, l, bestv[k], k, bestc[k])) { bestv[k] = v; bestc[k] = l; }
+            }
+        }
+        for (int q = 0; q < ni; ++q) inset[idx[q]] = 0;
+    }
+    info->rotations = rot;
+    info->status = status;
+    info->max_score_final = last;
+    info->off_final = or_offmass(A, n, normf);
+    *steps_out = steps;
+    free(bestv); free(bestc); free(taken); free(cand); free(pi); free(pj); free(inset); free(idx);
+    return 0;
+}

@@ -65,6 +65,7 @@ struct pjac_handle {
     DevBuf tcws;        // tensor-core product workspace
     DevBuf svdws;       // SVD: the m x n rotated matrix
     int coop_cap = 0;   // cap of the cooperative grids (0: the whole GPU)
+    int last_n = 0;     // order of the last workspace layout
     cudaEvent_t ev[4];
     std::mutex mu;
 };
@@ -83,6 +84,10 @@ extern "C" void pjac_default_opts(pjac_opts* o) {
     o->no_precondition = 0;
     o->seed = 0;
     o->refine_steps = 0;
+    o->fp32_sweeps = 0;
+    o->multi_pivot = 0;
+    o->multi_ratio = 0.0;
+    o->autotune = 1;
 }
 
 static int validate_opts(const pjac_opts* o) {
@@ -98,6 +103,11 @@ static int validate_opts(const pjac_opts* o) {
     if (o->no_precondition != 0 && o->no_precondition != 1)
         return set_err(PJAC_EINVAL, "opts.no_precondition must be 0 or 1");
     if (o->refine_steps < 0 || o->refine_steps > 8) return set_err(PJAC_EINVAL, "opts.refine_steps must be in [0,8]");
+    if (o->fp32_sweeps < 0 || o->fp32_sweeps > 100) return set_err(PJAC_EINVAL, "opts.fp32_sweeps must be in [0,100]");
+    if (o->multi_pivot < 0 || o->multi_pivot > 64) return set_err(PJAC_EINVAL, "opts.multi_pivot must be in [0,64]");
+    if (!(o->multi_ratio >= 0.0 && o->multi_ratio <= 1.0))
+        return set_err(PJAC_EINVAL, "opts.multi_ratio must be in [0,1]");
+    if (o->autotune != 0 && o->autotune != 1) return set_err(PJAC_EINVAL, "opts.autotune must be 0 or 1");
     return PJAC_OK;
 }
 
@@ -192,6 +202,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     size_t nn = (size_t)n * n;
+    h->last_n = n;
     const size_t nz = h->opts.refine_steps > 0 ? nn * 8 : 8;
     size_t sz[12] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
                      diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo), nz, 8};
@@ -289,11 +300,11 @@ static int newton_schulz(pjac_handle* h, double* Q, long long ldq, int n, int st
 // FP32 rotation moves column norms by a rounding unit).  So: X = fl64(Q0)
 // made orthogonal (Newton--Schulz), then a refinement pass on
 // B = X^T fl32(A) X that diagonalises it further, X <- X (I + D).  With
-// fp32_refine == false that pass is left out: the caller's FP64 first-order
-// refinement steps (pjac_opts.refine_steps) do its work.
+// fp32_refine == false that pass is left out.
 static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, double* Q, long long ldq,
                          SolveWs& w, cudaStream_t st, bool fp32_refine = true) {
-    CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, 40, h->coop_cap, st));
+    CK(diag_fp32(A, lda, n, w.Q0, w.d32, nullptr, h->opts.fp32_sweeps > 0 ? h->opts.fp32_sweeps : 40, h->coop_cap,
+                 st));
     CK(copy_f32_to_f64(w.Q0, n, Q, ldq, n, st));                        // X = fl64(Q0)
     if (!fp32_refine) return PJAC_OK;
     int r = newton_schulz(h, Q, ldq, n, 2, w, st);
@@ -304,7 +315,8 @@ static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, 
     r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
     if (r) return r;
     CK(symmetrize(w.Y, n, n, st));
-    CK(refine_fp32(w.Y, n, w.Q0, w.d32, 20, h->coop_cap, st));                        // D
+    const int rsw = h->opts.fp32_sweeps > 0 && h->opts.fp32_sweeps < 20 ? h->opts.fp32_sweeps : 20;
+    CK(refine_fp32(w.Y, n, w.Q0, w.d32, rsw, h->coop_cap, st));                        // D
     CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
     r = product(h, false, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);    // X D
     if (r) return r;
@@ -355,9 +367,8 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
         CK(copy_f32_to_f64(Q0, n, Q, ldq, n, st));
     } else {
         // after the final reorthogonalisation below, fl32(A) = Q Lambda Q^T
-        // to FP32 accuracy (with refinement steps requested, those take the
-        // place of the FP32 refinement pass)
-        int r = lowprec_basis(h, A, n, lda, Q, ldq, w, st, h->opts.refine_steps == 0);
+        // to FP32 accuracy
+        int r = lowprec_basis(h, A, n, lda, Q, ldq, w, st);
         if (r) return r;
     }
     int r = newton_schulz(h, Q, ldq, n, h->opts.ns_steps, w, st);
@@ -464,6 +475,13 @@ static int run_jacobi(pjac_handle* h, double* A1, long long lda1, int n, double*
     a.budget_ns = budget_ns(h->opts);
     a.info = dinfo;
     a.seed = h->opts.seed;
+    if (h->opts.multi_pivot >= 2) {
+        if (pivot != PJAC_PIVOT_GAP && pivot != PJAC_PIVOT_GREEDY)
+            return set_err(PJAC_EINVAL, "the multi-pivot variant needs the gap or the greedy rule");
+        if (n > 4096) return set_err(PJAC_EINVAL, "the multi-pivot variant takes n <= 4096 (n = %d)", n);
+        CK(launch_jacobi_multi(a, h->opts.multi_pivot, h->opts.multi_ratio, nullptr, st));
+        return PJAC_OK;
+    }
     int P = h->opts.cluster_size > 0 ? h->opts.cluster_size : jacobi_auto_cluster(n);
     while (P > 1 && (n + P - 1) / P < 8) P >>= 1;
     if ((n + P - 1) / P > 1024) return set_err(PJAC_EINVAL, "n = %d needs a larger cluster", n);
@@ -483,6 +501,7 @@ static int finish_info(pjac_handle* h, DevInfo* dinfo, pjac_info* info, cudaStre
         info->max_score = d.max_score;
         info->status = d.status;
         info->n = d.n;
+        info->steps = d.steps;
         info->ms_precond = info->ms_transform = info->ms_jacobi = 0.f;
         if (timed) {
             cudaEventElapsedTime(&info->ms_precond, h->ev[0], h->ev[1]);
@@ -670,7 +689,7 @@ extern "C" int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, 
             r = product_mnk(h, true, false, n, n, m, 1.0, B, ldb, B, ldb, 0.0, w.A1, n, st);
             if (r) return r;
             CK(symmetrize(w.A1, n, n, st));
-            r = lowprec_basis(h, w.A1, n, n, w.Vw, n, w, st, h->opts.refine_steps == 0);
+            r = lowprec_basis(h, w.A1, n, n, w.Vw, n, w, st);
             if (r) return r;
         }
         r = newton_schulz(h, w.Vw, n, n, h->opts.ns_steps, w, st);
@@ -742,6 +761,16 @@ extern "C" int pjac_svd_onesided(pjac_handle* h, const double* B, int m, int n, 
     return finish_info(h, w.info, info, st, true);
 }
 
+extern "C" int pjac_fp32_sweeps_done(pjac_handle* h, int* diag, int* refine) {
+    if (!h || h->last_n < 1) return set_err(PJAC_EINVAL, "no solve on this handle yet");
+    std::lock_guard<std::mutex> lk(h->mu);
+    SolveWs w;
+    int r = layout_ws(h, h->last_n, &w, 0);
+    if (r) return r;
+    CK(fp32_sweeps_done(w.d32, h->last_n, diag, refine));
+    return PJAC_OK;
+}
+
 extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     if (!h || n < 1 || n > PJAC_MAX_N) return -1;
     if (n == 1) return 0;
@@ -757,9 +786,7 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     // two products, 3I - Y and a copy per step
     c += (2 + ns) * (2 * P + 2);
     // fl32(A), T = fl32(A) X, B = X^T T, symmetrise, refinement, copy, X D, add
-    // (left out when FP64 refinement steps take the FP32 refinement's place)
-    if (h->opts.refine_steps == 0) c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
-    else c -= 2 * (2 * P + 2);
+    c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
     // transform (two products) and symmetrise, Jacobi, readout (two kernels)
     c += 2 * P + 1 + 1 + 2;
     // refinement steps: build and scale, Newton--Schulz (two products and

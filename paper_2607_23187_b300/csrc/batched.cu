@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <vector>
 #include "internal.h"
 
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(BT) b_diag32_kernel(const BatchDesc* desc, int
         }
         __syncthreads();
         double prev = -1.0;
-        for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        const int nsw = d.sweeps32 > 0 ? d.sweeps32 : max_sweeps;
+        for (int sweep = 0; sweep < nsw; ++sweep) {
             for (int r = 0; r < N - 1; ++r) {
                 for (int k = threadIdx.x; k < npairs; k += BT) {
                     int p, q;
@@ -281,7 +283,8 @@ __global__ void __launch_bounds__(BT) b_refine_kernel(const BatchDesc* desc, int
         if (t >= nb) break;
         BatchDesc d = desc[order[t]];
         const int n = d.n;
-        for (int step = 0; step < steps; ++step) {
+        const int nsteps = d.refine > 0 ? d.refine : steps;
+        for (int step = 0; step < nsteps; ++step) {
             // D, and its largest absolute row (= column) sum
             double mx = 0.0;
             for (int j = threadIdx.x; j < n; j += BT) {
@@ -378,12 +381,18 @@ int batched_launch_count(int no_precondition) { return no_precondition ? 4 : 6; 
 
 using namespace pjac;
 
+// the autotuner's choice for one (order bucket, pivot rule)
+struct TuneChoice { int refine, sweeps; float solves_per_s; };
+
 struct BatchState {
     void* dbuf = nullptr;     // device: descriptors, order, counters, per-problem workspace
     size_t dbytes = 0;
     void* hbuf = nullptr;     // pinned host staging
     size_t hbytes = 0;
     std::vector<void*> held;  // staging buffers read by captured graphs (freed on release)
+    cudaEvent_t ev[6] = {};   // stage boundaries of the last call made outside a capture
+    bool ev_made = false, ev_valid = false;
+    std::map<int, TuneChoice> tuned;   // autotuner: (order bucket, pivot) -> choice
 };
 
 // The batched workspace lives in a handle-independent cache keyed by the
@@ -397,6 +406,8 @@ void pjac_batched_release(const void* h) {
     std::lock_guard<std::mutex> lk(g_bmu);
     auto it = g_bstate.find(h);
     if (it == g_bstate.end()) return;
+    if (it->second.ev_made)
+        for (cudaEvent_t e : it->second.ev) cudaEventDestroy(e);
     if (it->second.dbuf) cudaFree(it->second.dbuf);
     if (it->second.hbuf) cudaFreeHost(it->second.hbuf);
     for (void* q : it->second.held) cudaFreeHost(q);
@@ -409,32 +420,22 @@ namespace pjac {
 int handle_opts(const pjac_handle* h, pjac_opts* o);
 }
 
-extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_off, const double* A,
-                                  const int64_t* w_off, double* W, const int64_t* v_off, double* V,
-                                  pjac_pivot pivot, double tol, pjac_info* infos, void* stream) {
-    if (!h || !n || !a_off || !A || !w_off || !W || !infos) return set_err(PJAC_EINVAL, "NULL argument");
-    if (V && !v_off) return set_err(PJAC_EINVAL, "v_off is NULL while V is not");
-    if (nb < 1) return set_err(PJAC_EINVAL, "nb = %d < 1", nb);
-    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
-    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
-    pjac_opts opts;
-    handle_opts(h, &opts);
-    if (opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
-        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+// The batched pipeline on nb problems, problem q with refinement steps
+// refine[q] and FP32 sweep cap sweeps[q].  Called with g_bmu held.
+static int batched_core(pjac_handle* h, const pjac_opts& opts, BatchState& bs, int nb, const int* n,
+                        const int64_t* a_off, const double* A, const int64_t* w_off, double* W,
+                        const int64_t* v_off, double* V, pjac_pivot pivot, double tol, pjac_info* infos,
+                        const int* refine, const int* sweeps, cudaStream_t st) {
+    (void)h;
     int max_n = 0;
     size_t ws = 0;
     for (int p = 0; p < nb; ++p) {
-        if (n[p] < 2 || n[p] > 1024) return set_err(PJAC_EINVAL, "n[%d] = %d outside [2, 1024]", p, n[p]);
-        if (a_off[p] < 0 || w_off[p] < 0 || (V && v_off[p] < 0)) return set_err(PJAC_EINVAL, "negative offset");
         max_n = std::max(max_n, n[p]);
         size_t nn = (size_t)n[p] * n[p];
         ws += a256(nn * 8) * 5 + a256((size_t)n[p] * 8) + a256(nn * 4) * 2 + a256(sizeof(DevInfo));
     }
     size_t hdr = a256(sizeof(BatchDesc) * nb) + a256(sizeof(int) * nb) + 256;
     size_t need = hdr + ws;
-    cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(g_bmu);
-    BatchState& bs = g_bstate[h];
     if (bs.dbytes < need) {
         // stream-ordered: growing never waits for other streams' work
         if (bs.dbuf) cudaFreeAsync(bs.dbuf, st);
@@ -498,6 +499,8 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
         d.Wout = W + w_off[q];
         d.Vout = V ? V + v_off[q] : nullptr;
         d.n = (int)m;
+        d.refine = refine[q];
+        d.sweeps32 = sweeps[q];
         h_desc[q] = d;
         h_order[q] = q;
     }
@@ -513,31 +516,194 @@ extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const in
     int ctas = std::min(nb, sms * 2);
     size_t smem32 = (size_t)2 * SMEM_N32 * SMEM_N32 * sizeof(float);
     BK(cudaFuncSetAttribute(b_diag32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    // stage boundaries, recorded outside a capture (pjac_batched_stage_ms)
+    if (!capturing && !bs.ev_made) {
+        for (cudaEvent_t& ev : bs.ev) BK(cudaEventCreate(&ev));
+        bs.ev_made = true;
+    }
+    auto mark = [&](int k) -> cudaError_t { return capturing ? cudaSuccess : cudaEventRecord(bs.ev[k], st); };
+    bs.ev_valid = false;
+    BK(mark(0));
     if (opts.no_precondition) {
         b_copyin_kernel<<<nb, BT, 0, st>>>(d_desc, nb);
         BK(cudaGetLastError());
+        BK(mark(1));
+        BK(mark(2));
+        BK(mark(3));
     } else {
         b_diag32_kernel<<<ctas, BT, smem32, st>>>(d_desc, nb, d_order, d_counters + 0, 40);
         BK(cudaGetLastError());
+        BK(mark(1));
         int ns = opts.ns_steps;
         b_precond_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 1, ns);
         BK(cudaGetLastError());
-        // one refinement step restores the FP32-accurate basis (see
-        // b_refine_kernel); opts.refine_steps adds more
-        b_refine_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 3,
-                                                              1 + opts.refine_steps);
+        BK(mark(2));
+        // refinement steps per problem (at least one, which restores the
+        // FP32-accurate basis; see b_refine_kernel)
+        b_refine_kernel<<<std::min(nb, sms * 4), BT, 0, st>>>(d_desc, nb, d_order, d_counters + 3, 1);
         BK(cudaGetLastError());
+        BK(mark(3));
     }
     long long budget = (long long)((opts.time_budget_s > 0 ? opts.time_budget_s : 600.0) * 1e9);   // ns
     BK(launch_jacobi_batched(d_desc, nb, d_order, d_counters + 2, (int)pivot, (int)opts.stop, tol, 25, budget,
                              max_n, std::min(nb, sms * 2), opts.seed, st));
+    BK(mark(4));
     BK(launch_readout_batched(d_desc, nb, max_n, st));
     BK(launch_info_batched(d_desc, nb, infos, st));   // keep batched_launch_count() in step
+    BK(mark(5));
+    bs.ev_valid = !capturing;
 #undef BK
     if (capturing) {
         bs.held.push_back(bs.hbuf);
         bs.hbuf = nullptr;
         bs.hbytes = 0;
+    }
+    return PJAC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched form.  Per order bucket (n < 32, < 64, < 128,
+// <= 256, > 256) and pivot rule it chooses the refinement steps (1, 2 or 3)
+// and the FP32 sweep cap (12 or 40) of the problems in that bucket: more
+// refinement moves work from the latency-bound Jacobi chain onto the CTA's
+// FP64 products, fewer FP32 sweeps shorten stage 1 at the cost of a rougher
+// basis.  On the first call outside a stream capture that meets a bucket not
+// yet tuned, up to 32 of the call's own problems of that bucket are solved
+// with every candidate, timed on the device, and the fastest candidate is
+// kept in the handle's cache; later calls (and graphs captured after it)
+// reuse it.  opts.autotune = 0 skips it (refinement 1 + opts.refine_steps,
+// sweep cap opts.fp32_sweeps or 40).
+// ---------------------------------------------------------------------------
+static int order_bucket(int n) { return n < 32 ? 0 : n < 64 ? 1 : n < 128 ? 2 : n <= 256 ? 3 : 4; }
+
+static const int kCands[6][2] = {{1, 40}, {2, 40}, {3, 40}, {1, 12}, {2, 12}, {3, 12}};
+
+static int tune_bucket(pjac_handle* h, const pjac_opts& opts, BatchState& bs, const std::vector<int>& idx,
+                       const int* n, const int64_t* a_off, const double* A, pjac_pivot pivot, double tol,
+                       cudaStream_t st, TuneChoice* out) {
+    const int m = (int)idx.size();
+    std::vector<int> ns(m);
+    std::vector<int64_t> ao(m), wo(m), vo(m);
+    int64_t wsum = 0, vsum = 0;
+    for (int q = 0; q < m; ++q) {
+        ns[q] = n[idx[q]];
+        ao[q] = a_off[idx[q]];
+        wo[q] = wsum;
+        vo[q] = vsum;
+        wsum += ns[q];
+        vsum += (int64_t)ns[q] * ns[q];
+    }
+    double* W = nullptr;
+    double* V = nullptr;
+    pjac_info* inf = nullptr;
+    cudaError_t e = cudaMallocAsync(&W, sizeof(double) * wsum, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&V, sizeof(double) * vsum, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&inf, sizeof(pjac_info) * m, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (W) cudaFreeAsync(W, st);
+        if (V) cudaFreeAsync(V, st);
+        return set_err(PJAC_ENOMEM, "autotuner buffers: %s", cudaGetErrorString(e));
+    }
+    float best_ms = -1.f;
+    int best = 0;
+    int r = PJAC_OK;
+    for (int c = 0; c < 6 && r == PJAC_OK; ++c) {
+        std::vector<int> rf(m, kCands[c][0]), sw(m, kCands[c][1]);
+        r = batched_core(h, opts, bs, m, ns.data(), ao.data(), A, wo.data(), W, vo.data(), V, pivot, tol, inf,
+                         rf.data(), sw.data(), st);
+        if (r) break;
+        if (cudaEventSynchronize(bs.ev[5]) != cudaSuccess) { r = cuda_err(cudaGetLastError(), "tuning"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, bs.ev[0], bs.ev[5]);
+        if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaFreeAsync(W, st);
+    cudaFreeAsync(V, st);
+    cudaFreeAsync(inf, st);
+    if (r) return r;
+    out->refine = kCands[best][0];
+    out->sweeps = kCands[best][1];
+    out->solves_per_s = best_ms > 0.f ? 1000.f * m / best_ms : 0.f;
+    return PJAC_OK;
+}
+
+extern "C" int pjac_solve_batched(pjac_handle* h, int nb, const int* n, const int64_t* a_off, const double* A,
+                                  const int64_t* w_off, double* W, const int64_t* v_off, double* V,
+                                  pjac_pivot pivot, double tol, pjac_info* infos, void* stream) {
+    if (!h || !n || !a_off || !A || !w_off || !W || !infos) return set_err(PJAC_EINVAL, "NULL argument");
+    if (V && !v_off) return set_err(PJAC_EINVAL, "v_off is NULL while V is not");
+    if (nb < 1) return set_err(PJAC_EINVAL, "nb = %d < 1", nb);
+    if (pivot < PJAC_PIVOT_GAP || pivot > PJAC_PIVOT_RANDOM) return set_err(PJAC_EINVAL, "bad pivot");
+    if (!(tol >= 0.0)) return set_err(PJAC_EINVAL, "tol must be >= 0");
+    pjac_opts opts;
+    handle_opts(h, &opts);
+    if (opts.stop == PJAC_STOP_LIBOUND && pivot != PJAC_PIVOT_GAP)
+        return set_err(PJAC_EINVAL, "PJAC_STOP_LIBOUND needs the gap rule");
+    for (int p = 0; p < nb; ++p) {
+        if (n[p] < 2 || n[p] > 1024) return set_err(PJAC_EINVAL, "n[%d] = %d outside [2, 1024]", p, n[p]);
+        if (a_off[p] < 0 || w_off[p] < 0 || (V && v_off[p] < 0)) return set_err(PJAC_EINVAL, "negative offset");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ec = cudaStreamIsCapturing(st, &cap);
+    if (ec != cudaSuccess) return cuda_err(ec, "cudaStreamIsCapturing");
+    std::lock_guard<std::mutex> lk(g_bmu);
+    BatchState& bs = g_bstate[h];
+    const int base_refine = 1 + opts.refine_steps;
+    const int base_sweeps = opts.fp32_sweeps > 0 ? opts.fp32_sweeps : 40;
+    if (opts.autotune && !opts.no_precondition && cap == cudaStreamCaptureStatusNone) {
+        std::vector<int> members[5];
+        for (int p = 0; p < nb; ++p) members[order_bucket(n[p])].push_back(p);
+        for (int b = 0; b < 5; ++b) {
+            const int key = b * 16 + (int)pivot;
+            if (members[b].size() < 8 || bs.tuned.count(key)) continue;
+            std::vector<int> sample;
+            const size_t step = std::max<size_t>(1, members[b].size() / 32);
+            for (size_t q = 0; q < members[b].size() && sample.size() < 32; q += step) sample.push_back(members[b][q]);
+            TuneChoice c;
+            int r = tune_bucket(h, opts, bs, sample, n, a_off, A, pivot, tol, st, &c);
+            if (r) return r;
+            bs.tuned[key] = c;
+        }
+    }
+    std::vector<int> rf(nb), sw(nb);
+    for (int p = 0; p < nb; ++p) {
+        auto it = opts.autotune ? bs.tuned.find(order_bucket(n[p]) * 16 + (int)pivot) : bs.tuned.end();
+        rf[p] = (it != bs.tuned.end()) ? it->second.refine : base_refine;
+        sw[p] = (it != bs.tuned.end()) ? it->second.sweeps : base_sweeps;
+    }
+    return batched_core(h, opts, bs, nb, n, a_off, A, w_off, W, v_off, V, pivot, tol, infos, rf.data(), sw.data(),
+                        st);
+}
+
+extern "C" int pjac_batched_tuning(pjac_handle* h, int bucket, pjac_pivot pivot, int* refine, int* fp32_sweeps,
+                                   float* sample_solves_per_s) {
+    if (!h || bucket < 0 || bucket > 4) return set_err(PJAC_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bstate.find(h);
+    if (it == g_bstate.end()) return set_err(PJAC_EINVAL, "no batched call on this handle yet");
+    auto c = it->second.tuned.find(bucket * 16 + (int)pivot);
+    if (c == it->second.tuned.end()) return set_err(PJAC_EINVAL, "bucket %d not tuned", bucket);
+    if (refine) *refine = c->second.refine;
+    if (fp32_sweeps) *fp32_sweeps = c->second.sweeps;
+    if (sample_solves_per_s) *sample_solves_per_s = c->second.solves_per_s;
+    return PJAC_OK;
+}
+
+extern "C" int pjac_batched_stage_ms(pjac_handle* h, float* ms) {
+    if (!h || !ms) return set_err(PJAC_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bstate.find(h);
+    if (it == g_bstate.end() || !it->second.ev_valid)
+        return set_err(PJAC_EINVAL, "no batched call outside a stream capture on this handle yet");
+    BatchState& bs = it->second;
+    cudaError_t e = cudaEventSynchronize(bs.ev[5]);
+    if (e != cudaSuccess) return cuda_err(e, "cudaEventSynchronize");
+    for (int k = 0; k < 5; ++k) {
+        e = cudaEventElapsedTime(&ms[k], bs.ev[k], bs.ev[k + 1]);
+        if (e != cudaSuccess) return cuda_err(e, "cudaEventElapsedTime");
     }
     return PJAC_OK;
 }

@@ -22,6 +22,13 @@ namespace cg = cooperative_groups;
 
 namespace pjac {
 
+// Sweeps made by the last diag32 (which = 0) and refine32 (which = 1) launch
+// on a workspace: two ints at its end, outside every area the kernels use.
+__host__ __device__ inline int* sweep_slot(float* ws, int n) {
+    const long long npad = ((n + 31) / 32) * 32;
+    return reinterpret_cast<int*>(ws + (4 * npad * npad + 6 * npad + 64) - 4);
+}
+
 // new position -> old position (m = npad/2 pairs)
 __device__ __forceinline__ int tour_sigma(int p, int m) {
     if (p == 0) return 0;
@@ -147,6 +154,7 @@ __global__ void __launch_bounds__(256) diag32_coop_kernel(const double* __restri
     const int ntiles = 2 * T * T;
     int cur = 0;
     double prev = -1.0;
+    int done = max_sweeps;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < npad - 1; ++r) {
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
@@ -185,9 +193,10 @@ __global__ void __launch_bounds__(256) diag32_coop_kernel(const double* __restri
             other[0] = 0.0;
             other[1] = 0.0;
         }
-        if (stop) break;
+        if (stop) { done = sweep + 1; break; }
         grid.sync();   // the other slot is zero before anyone adds to it
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_slot(Ab0, n)[0] = done;
     // Q0 (n x n, ld n).  After whole sweeps (npad-1 rounds each) every
     // player is back at its own position, so the first n positions are the
     // real indices; padding indices are zero rows/columns that only ever
@@ -328,6 +337,7 @@ __global__ void __launch_bounds__(256) refine32_coop_kernel(const double* __rest
     const int ntiles = 2 * T * T;
     int cur = 0;
     double prev = -1.0;
+    int done = max_sweeps;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < npad - 1; ++r) {
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
@@ -371,9 +381,10 @@ __global__ void __launch_bounds__(256) refine32_coop_kernel(const double* __rest
             other[0] = 0.0;
             other[1] = 0.0;
         }
-        if (stop) break;
+        if (stop) { done = sweep + 1; break; }
         grid.sync();
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sweep_slot(ws, n)[1] = done;
     // whole sweeps bring every player back to its own seat: D is in the
     // original column order
     const float* Dc = Db[cur];
@@ -442,4 +453,16 @@ cudaError_t preload_diag32_kernels() {
     return e;
 }
 
+}  // namespace pjac
+
+namespace pjac {
+// Sweeps made by the last diag32 / refine32 launches on workspace ws (host
+// copy; synchronises the device).
+cudaError_t fp32_sweeps_done(float* ws, int n, int* diag, int* refine) {
+    int v[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(v, sweep_slot(ws, n), sizeof(v), cudaMemcpyDeviceToHost);
+    if (diag) *diag = v[0];
+    if (refine) *refine = v[1];
+    return e;
+}
 }  // namespace pjac

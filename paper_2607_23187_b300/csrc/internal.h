@@ -16,6 +16,7 @@ struct DevInfo {
     double max_score;      // last selected score
     int status;            // pjac_status
     int n;
+    long long steps;       // selection steps (rotations, except for the multi-pivot variant)
 };
 
 struct JacArgs {
@@ -51,6 +52,8 @@ struct BatchDesc {
     double* Vout;          // caller's V of this problem (may be null)
     DevInfo* info;
     int n;
+    int refine;            // refinement steps (stage 2b)
+    int sweeps32;          // FP32 sweep cap (stage 1)
     int pad;
 };
 
@@ -106,6 +109,7 @@ cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st
 cudaError_t diag_fp32(const double* A, long long lda, int n, float* Q0, float* ws, int* iws,
                       int max_sweeps, int max_grid, cudaStream_t st);
 size_t diag_fp32_ws_floats(int n);
+cudaError_t fp32_sweeps_done(float* ws, int n, int* diag, int* refine);
 // refinement of an FP32 eigenbasis on B = X^T fl32(A) X; Dout: X (I + D)
 cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_sweeps, int max_grid,
                         cudaStream_t st);
@@ -113,6 +117,10 @@ cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_
 void handle_set_coop_cap(pjac_handle* h, int max_grid);
 cudaError_t round_to_fp32(const double* src, long long lds, double* dst, long long ldd, int n, cudaStream_t st);
 cudaError_t add_f64(double* X, long long ldx, const double* Y, long long ldy, int n, cudaStream_t st);
+
+// multi.cu: the multi-pivot variant (one CTA per problem)
+cudaError_t launch_jacobi_multi(const JacArgs& a, int K, double ratio, long long* steps_out, cudaStream_t st);
+cudaError_t preload_multi_kernels();
 
 // svd.cu: readout of the one-sided Jacobi SVD
 cudaError_t check_finite_rect(const double* A, long long lda, int m, int n, int* d_flag, cudaStream_t st);

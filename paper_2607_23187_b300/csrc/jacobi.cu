@@ -1098,6 +1098,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         inf.max_score = last_score;
         inf.status = status;
         inf.n = n;
+        inf.steps = rot;
         *a.info = inf;
     }
 }
@@ -1329,6 +1330,7 @@ __global__ void info_batched_kernel(const BatchDesc* desc, int nb, pjac_info* in
     o.ms_precond = 0.f;
     o.ms_transform = 0.f;
     o.ms_jacobi = 0.f;
+    o.steps = d.steps;
     infos[p] = o;
 }
 
@@ -1345,6 +1347,7 @@ __global__ void info_single_kernel(const DevInfo* src, pjac_info* dst) {
     o.ms_precond = 0.f;
     o.ms_transform = 0.f;
     o.ms_jacobi = 0.f;
+    o.steps = d.steps;
     *dst = o;
 }
 

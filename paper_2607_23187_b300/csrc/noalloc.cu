@@ -149,6 +149,7 @@ extern "C" int pjac_solve_preconditioned_noalloc(double* A1, int n, int lda1, co
         info->max_score = d.max_score;
         info->status = d.status;
         info->n = d.n;
+        info->steps = d.steps;
         info->ms_precond = info->ms_transform = info->ms_jacobi = 0.f;
     }
     return d.status == PJAC_OK ? PJAC_OK

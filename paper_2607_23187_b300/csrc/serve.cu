@@ -193,6 +193,7 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
     if (el == cudaSuccess) el = preload_jacobi_kernels();
     if (el == cudaSuccess) el = preload_svd_kernels();
     if (el == cudaSuccess) el = preload_os_kernels();
+    if (el == cudaSuccess) el = preload_multi_kernels();
     if (el != cudaSuccess) {
         delete sv;
         return cuda_err(el, "serve: loading the kernels");
@@ -202,7 +203,11 @@ extern "C" int pjac_serve_create(pjac_server** s, const pjac_serve_opts* o) {
     for (int li = 0; li < d.max_slots; ++li) {
         Lane& L = sv->lanes[li];
         L.hi = li < n_hi;
-        int r = pjac_create(&L.h, &d.solver);
+        // no autotuning on the lanes: a request's result must not depend on
+        // which micro-batch (and which tuning state) it lands in
+        pjac_opts lo = d.solver;
+        lo.autotune = 0;
+        int r = pjac_create(&L.h, &lo);
         // a served request's preconditioner must start beside running solves:
         // its cooperative kernels use at most 64 CTAs instead of the whole GPU
         if (r == PJAC_OK) handle_set_coop_cap(L.h, 64);

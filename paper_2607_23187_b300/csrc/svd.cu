@@ -349,6 +349,7 @@ __global__ void __launch_bounds__(OS_NT) svd_onesided_kernel(double* B, int m, i
         d.max_score = last;
         d.status = status;
         d.n = n;
+        d.steps = rot;
         *info = d;
     }
 }

@@ -34,6 +34,7 @@ EXPORTS = (
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
     "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
     "pjac_product_launch_count", "pjac_eig_lowprec", "pjac_svd", "pjac_svd_onesided", "pjac_probe_fp64",
+    "pjac_batched_stage_ms", "pjac_batched_tuning", "pjac_fp32_sweeps_done",
 )
 
 
@@ -49,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("transform", ctypes.c_int), ("ns_steps", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("time_budget_s", ctypes.c_double),
                 ("no_precondition", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("refine_steps", ctypes.c_int)]
+                ("refine_steps", ctypes.c_int), ("fp32_sweeps", ctypes.c_int),
+                ("multi_pivot", ctypes.c_int), ("multi_ratio", ctypes.c_double), ("autotune", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +59,7 @@ class Info(ctypes.Structure):
                 ("off_rel", ctypes.c_double), ("max_score", ctypes.c_double),
                 ("status", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("ms_precond", ctypes.c_float), ("ms_transform", ctypes.c_float),
-                ("ms_jacobi", ctypes.c_float)]
+                ("ms_jacobi", ctypes.c_float), ("steps", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -108,6 +110,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_svd_onesided.argtypes = [vp, vp, i, i, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
         L.pjac_probe_fp64.argtypes = [ctypes.POINTER(d), vp]
         L.pjac_probe_fp64.restype = ctypes.c_int
+        L.pjac_batched_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+        L.pjac_batched_stage_ms.restype = ctypes.c_int
+        L.pjac_batched_tuning.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                          ctypes.POINTER(ctypes.c_float)]
+        L.pjac_batched_tuning.restype = ctypes.c_int
+        L.pjac_fp32_sweeps_done.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.pjac_fp32_sweeps_done.restype = ctypes.c_int
         L.pjac_solve_batched.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, i, d, vp, vp]
         L.pjac_serve_default_opts.argtypes = [ctypes.POINTER(ServeOpts)]
         L.pjac_serve_default_opts.restype = None

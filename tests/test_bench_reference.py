@@ -24,6 +24,7 @@ def _run(*extra):
     ("product", ["--n", "512"], "PRODUCT_METRIC", "products/s"),
     ("serving", ["--requests", "30", "--ref-rotations", "2000"], "SERVING_METRIC", "solves/s"),
     ("batched", [], "BATCHED_METRIC", "solves/s"),
+    ("cfg2", ["--ref-rotations", "3000"], "METRIC", "solves/s"),
 ])
 def test_reference_arm_line(workload, extra, metric_key, unit):
     sys.path.insert(0, ROOT)
@@ -36,3 +37,14 @@ def test_reference_arm_line(workload, extra, metric_key, unit):
     assert d["e2e"] == {"value": d["value"], "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     if workload == "serving":
         assert d["latency_ms"]["p99"] >= d["latency_ms"]["p50"] > 0
+
+
+def test_reference_and_cpu_baseline_share_one_rule():
+    """Both oracle legs extrapolate a timed sample to the same rotation count
+    (the oracle's own count for the workload and preconditioner)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = _run("--workload", "cfg2", "--ref-rotations", "3000")
+    need = bench.ORACLE_SOLVE_ROTATIONS[("cfg2", 1024, 3)]
+    assert ("extrapolated to %d rotations" % need) in d["cpu_baseline"]["sample"]
+    assert "refinement" in d["config"]["preconditioner"]

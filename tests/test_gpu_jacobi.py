@@ -272,3 +272,32 @@ def test_solve_without_preconditioner(pj, h):
     assert st == 0 and info["rotations"] == r["rotations"]
     assert np.array_equal(gw.cpu().numpy(), w)
     assert np.array_equal(gv.cpu().numpy(), v)
+
+
+@pytest.mark.parametrize("K,ratio,pivot", [(1, 0.0, "gap"), (4, 0.0, "gap"), (16, 0.0, "gap"), (32, 0.0, "gap"),
+                                           (16, 0.01, "gap"), (16, 0.0, "greedy")])
+def test_multi_pivot_parity(pj, h, K, ratio, pivot):
+    """The multi-pivot variant: the same accepted pivot sets, rotations,
+    crossing-block updates and cache updates as the oracle, bit for bit;
+    K = 1 is Algorithm 1."""
+    p, q0, q, a1 = preconditioned("cfg2", n=300)
+    r = oracle.jacobi_multi(a1, q, pivot=pivot, tol=1e-15, K=K, ratio=ratio)
+    w, v = oracle.readout(r["a"], r["v"])
+    gw, gv, ga, info, st = gpu_run(pj, h, a1, q, pivot, 1e-15, multi_pivot=max(K, 2) if K > 1 else 0,
+                                   multi_ratio=ratio)
+    if K == 1:
+        r1, w1, v1 = oracle_run("cfg2_300", a1, q, pivot, 1e-15)
+        assert r["rotations"] == r1["rotations"] and np.array_equal(r["a"], r1["a"])
+    assert st == 0 and r["status"] == 0
+    assert info["steps"] == r["steps"]
+    assert_bit_parity(r, w, v, gw, gv, ga, info)
+
+
+@pytest.mark.parametrize("kind,n", [("equal", 70), ("int", 130), ("tridiag", 130)])
+def test_multi_pivot_ties_parity(pj, h, kind, n):
+    a = ties_matrix(kind, n)
+    r = oracle.jacobi_multi(a, None, pivot="gap", tol=1e-15, K=16)
+    w, v = oracle.readout(r["a"], r["v"])
+    gw, gv, ga, info, st = gpu_run(pj, h, a, None, "gap", 1e-15, multi_pivot=16)
+    assert st == 0 and info["steps"] == r["steps"]
+    assert_bit_parity(r, w, v, gw, gv, ga, info)

@@ -387,3 +387,70 @@ def test_random_rule_follows_its_draws_and_converges():
     # the greedy-type rules need fewer rotations than uniform draws
     rg = oracle.jacobi(a1, q, pivot="gap", tol=1e-15)
     assert rg["rotations"] < r["rotations"]
+
+
+# --------------------------------------------------------------------------
+# the multi-pivot variant
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("pivot", ["gap", "greedy"])
+def test_multi_pivot_k1_is_algorithm1(pivot):
+    p = pin.config_problem("cfg2", n=120)
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    r = oracle.jacobi(a1, q, pivot=pivot, tol=1e-15)
+    m = oracle.jacobi_multi(a1, q, pivot=pivot, tol=1e-15, K=1)
+    assert m["rotations"] == r["rotations"] == m["steps"]
+    assert np.array_equal(m["a"], r["a"]) and np.array_equal(m["v"], r["v"])
+
+
+def test_multi_pivot_converges_with_fewer_steps():
+    """Disjoint pivots per step: the known spectrum is reached, the
+    accumulated V stays orthogonal and diagonalises A, the trace is kept, and
+    the steps fall well below the rotations."""
+    p = pin.config_problem("cfg2", n=200)
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    base = oracle.jacobi(a1, q, pivot="gap", tol=1e-15)
+    for K in (8, 32):
+        m = oracle.jacobi_multi(a1, q, pivot="gap", tol=1e-15, K=K)
+        assert m["status"] == 0
+        w, v = oracle.readout(m["a"], m["v"])
+        assert np.max(np.abs(w - p.lam)) <= 1e-13 * p.norm2
+        assert np.linalg.norm(v.T @ v - np.eye(p.n)) <= 1e-12
+        assert np.linalg.norm(p.a @ v - v * w) / np.linalg.norm(p.a) <= 1e-12
+        assert abs(np.trace(m["a"]) - np.trace(a1)) <= 1e-13 * np.abs(a1).sum()
+        assert m["steps"] * (K // 8) < m["rotations"]
+        assert m["rotations"] <= 1.1 * base["rotations"]
+
+
+def test_multi_pivot_step_brute_force():
+    """One step checked by hand: the accepted pivots are the non-conflicting
+    heads of the K best rows, in rank order, each rotated as Algorithm 1
+    rotates it."""
+    rng = np.random.default_rng(31)
+    b = rng.standard_normal((12, 12))
+    a = b + b.T
+    K = 6
+    m = oracle.jacobi_multi(a, None, pivot="gap", tol=0.0, K=K, max_rot=1)
+    # brute force: row bests, rank, accept, rotate in order
+    n = 12
+    heads = []
+    for k in range(n):
+        best, col = -1.0, None
+        for l in range(n):
+            if l != k:
+                v = oracle.gap_score(a[k, k], a[l, l], a[k, l])
+                if v > best:
+                    best, col = v, l
+        heads.append((best, k, col))
+    ranked = sorted(heads, key=lambda t: (-t[0], t[1]))[:K]
+    used, piv = set(), []
+    for v, k, l in ranked:
+        i, j = min(k, l), max(k, l)
+        if i in used or j in used:
+            continue
+        used |= {i, j}
+        piv.append((i, j))
+    ref = a.copy()
+    for i, j in piv:
+        oracle.rotate(ref, i, j)
+    assert m["steps"] == 1 and m["rotations"] == len(piv) >= 2
+    assert np.array_equal(m["a"], ref)
