@@ -181,10 +181,20 @@ def run_reference(args, ws, rank):
     values = []
     t_pre = None
     sample = ""
+    # the preconditioner (fixed work) is timed in full once; every step
+    # re-times a rotation sample of the oracle's Algorithm 1 and adds it
+    t_solve, t_pre, rate, sample = oracle_sample(p, args)
+    import oracle
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
+    need = ORACLE_SOLVE_ROTATIONS.get((args.workload, n, args.refine), 1.8 * n * (n - 1) / 2)
+    per_step = 2000 if n > 1024 else 10000
     for step in range(args.warmup + args.steps):
-        t_solve, t_pre, rate, sample = oracle_sample(p, args)
+        t0 = time.perf_counter()
+        r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=per_step)
+        rate_s = r["rotations"] / max(time.perf_counter() - t0, 1e-9)
         if step >= args.warmup:
-            values.append(1.0 / t_solve)
+            values.append(1.0 / (t_pre + need / rate_s))
+    sample += "; each timed step re-measures %d rotations and adds the preconditioner's time" % per_step
     v = float(np.median(values))
     unit = "solves/s"
     out = {"metric": METRIC, "value": v, "unit": unit, "n_gpus": ws, "steps": args.steps,
@@ -207,7 +217,7 @@ def run_reference(args, ws, rank):
 # steps, gap rule, off-diagonal stop 1e-15), measured once on the CPU with
 # oracle.solve; both oracle legs (the cpu_baseline of our line and the
 # reference arm) extrapolate a timed sample of rotations to these counts.
-ORACLE_SOLVE_ROTATIONS = {("cfg2", 1024, 0): 924672, ("cfg2", 1024, 3): 83968}
+ORACLE_SOLVE_ROTATIONS = {("cfg2", 1024, 0): 924672, ("cfg2", 1024, 3): 83968, ("cfg3", 4096, 3): 94208}
 
 
 def preconditioner_label(args):
@@ -225,23 +235,30 @@ def oracle_sample(p, args):
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a), refine_steps=args.refine)
+    q, a1 = oracle.precondition(p.a, oracle.q0_fp32(p.a))
     t1 = time.perf_counter()
-    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=args.ref_rotations)
+    t_ref = 0.0
+    if args.refine:
+        a1, q = oracle.refine_step(a1, q)
+        t_ref = (time.perf_counter() - t1) * args.refine    # one step timed, the others alike
     t2 = time.perf_counter()
-    rate = r["rotations"] / max(t2 - t1, 1e-9)
+    budget = args.ref_rotations or (40000 if p.n <= 1024 else 8000)
+    r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15, max_rot=budget)
+    t3 = time.perf_counter()
+    rate = r["rotations"] / max(t3 - t2, 1e-9)
     key = (args.workload, p.n, args.refine)
     need = ORACLE_SOLVE_ROTATIONS.get(key)
     how = "the oracle's own rotation count for this workload (measured once with oracle.solve)"
     if need is None:
         need = 1.8 * p.n * (p.n - 1) / 2
         how = "1.8 sweeps of n(n-1)/2 rotations (no stored oracle count for this workload)"
-    t_solve = (t1 - t0) + need / rate
-    sample = ("oracle preconditioner in full (LAPACK FP32 eigh, FP64 Newton-Schulz, Q^T A Q, %d refinement "
-              "steps; numpy on %d threads), then %d gap-rule rotations of the C oracle (one thread) at %.0f "
-              "rotations/s, extrapolated to %d rotations: %s"
-              % (args.refine, os.cpu_count(), r["rotations"], rate, need, how))
-    return t_solve, t1 - t0, rate, sample
+    t_pre = (t1 - t0) + t_ref
+    t_solve = t_pre + need / rate
+    sample = ("oracle preconditioner (LAPACK FP32 eigh, FP64 Newton-Schulz, Q^T A Q; numpy on %d threads) in "
+              "full, %d refinement steps (one timed, %.1f s each), then %d gap-rule rotations of the C oracle "
+              "(one thread) at %.0f rotations/s, extrapolated to %d rotations: %s"
+              % (os.cpu_count(), args.refine, t_ref / max(args.refine, 1), r["rotations"], rate, need, how))
+    return t_solve, t_pre, rate, sample
 
 
 def cpu_baseline_single(p, args):
@@ -339,20 +356,25 @@ def run_ours(args, ws, rank, local):
         timed("greedy", pivot="greedy")
         timed("gap_theorem1_stop", stop="libound", tol=tol_li)
         extras["gap_theorem1_stop"].update({"tol": tol_li, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1"})
-        if args.refine:
+        if args.refine and n <= 1024:
             timed("paper_preconditioner", refine=0)
             timed("paper_preconditioner_theorem1_stop", refine=0, stop="libound", tol=tol_li)
-        timed("plain_fp64_path", refine=0, transform="fp64")
-        extras["plain_fp64_path"]["what"] = "FP64 CUDA-core products, no refinement, the same Jacobi kernel"
+        if time.perf_counter() - t_start < 900:
+            timed("plain_fp64_path", refine=0, transform="fp64")
+            extras["plain_fp64_path"]["what"] = ("the paper's preconditioner (no refinement, FP32 sweep cap %s) with "
+                                                 "FP64 CUDA-core products, the same Jacobi kernel"
+                                                 % (args.fp32_sweeps or 40))
         if not args.no_4096 and n != 4096:
             p4 = workload_problem("cfg3")
             a4 = torch.tensor(p4.a, device=dev)
             tl4 = 1e-13 * p4.norm2 / float(np.linalg.norm(p4.a))
             timed("cfg3_n4096_theorem1_stop", mat=a4, prob=p4, stop="libound", tol=tl4)
             extras["cfg3_n4096_theorem1_stop"].update({"tol": tl4, "guarantee": "|dlambda| <= 1e-13 ||A||_2 by Theorem 1"})
-            if time.perf_counter() - t_start < 700:
-                timed("cfg3_n4096_full_solve", mat=a4, prob=p4)
+            timed("cfg3_n4096_full_solve", mat=a4, prob=p4)
             del a4
+        if n == 4096:
+            p2 = workload_problem("cfg2")
+            timed("cfg2_n1024_full_solve", mat=torch.tensor(p2.a, device=dev), prob=p2)
         h.set_opts(transform=args.transform, cluster_size=args.cluster, refine_steps=args.refine,
                    fp32_sweeps=args.fp32_sweeps)
 
@@ -1083,22 +1105,72 @@ def run_hilbert(args, ws, rank, local):
     h.close()
 
 
+# ----------------------------------------------------------------------------
+# the multi-pivot variant against Algorithm 1 (one pivot per step)
+# ----------------------------------------------------------------------------
+MULTI_METRIC = "Jacobi rotations/s of the multi-pivot variant (K best row heads per step, gap rule)"
+
+
+def run_multi(args, ws, rank, local):
+    import torch
+    import pjac_inputs as pin
+    from paper_2607_23187_b300 import pjac
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n or 1024
+    p = pin.config_problem("cfg2", n=n)
+    h = pjac.Handle(refine_steps=args.refine)
+    q, a1 = pjac.pjac_precondition(h, torch.tensor(p.a, device=dev))
+    rows = {}
+    clk = Clocks(local)
+    clk.start()
+    for K in (0, 8, 16, 32, 64):
+        h.set_opts(transform="fp64", multi_pivot=K)
+        a = a1.clone()
+        pjac.pjac_solve_preconditioned(h, a, q, "gap", 1e-15)          # warm-up
+        a = a1.clone()
+        torch.cuda.synchronize()
+        w, v, info, st = pjac.pjac_solve_preconditioned(h, a, q, "gap", 1e-15)
+        torch.cuda.synchronize()
+        err = float(np.max(np.abs(w.cpu().numpy() - p.lam)) / p.norm2)
+        rows["K=%d" % max(K, 1)] = {"kernel": "jacobi_multi_kernel" if K > 1 else "jacobi_single_kernel",
+                                    "rotations": info["rotations"], "steps": info["steps"],
+                                    "jacobi_ms": info["ms_jacobi"],
+                                    "us_per_rotation": 1000.0 * info["ms_jacobi"] / max(info["rotations"], 1),
+                                    "us_per_step": 1000.0 * info["ms_jacobi"] / max(info["steps"], 1),
+                                    "rel_eig_err": err, "status": st}
+    clocks = clk.stop()
+    best = max((r for k, r in rows.items() if k != "K=1"), key=lambda r: r["rotations"] / r["jacobi_ms"])
+    out = {"metric": MULTI_METRIC, "value": 1000.0 * best["rotations"] / best["jacobi_ms"], "unit": "rotations/s",
+           "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": best["jacobi_ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "cfg2 recipe, n = %d, GPU preconditioner (%d refinement steps), gap rule, "
+                                  "off-diagonal stop 1e-15; K = 1 is Algorithm 1 on the cluster kernel" % (n, args.refine),
+                      "n": n},
+           "by_K": rows,
+           "single_pivot_rotations_per_s": 1000.0 * rows["K=1"]["rotations"] / rows["K=1"]["jacobi_ms"],
+           "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg2",
-                    choices=["cfg2", "cfg3", "batched", "product", "serving", "p1", "svd", "hilbert"])
+    ap.add_argument("--workload", default="cfg3",
+                    choices=["cfg2", "cfg3", "batched", "product", "serving", "p1", "svd", "hilbert", "multi"])
     ap.add_argument("--refine", type=int, default=3, help="first-order refinement steps (an extension)")
-    ap.add_argument("--fp32-sweeps", type=int, default=0, help="sweep cap of the FP32 eigenbasis (0: 40)")
+    ap.add_argument("--fp32-sweeps", type=int, default=12, help="sweep cap of the FP32 eigenbasis (0: 40)")
     ap.add_argument("--no-4096", action="store_true", help="leave out the n=4096 extra solve")
     ap.add_argument("--p1-chunk", type=int, default=1000, help="P1: rotations between error measurements")
     ap.add_argument("--n", type=int, default=None, help="order of the workload recipe (default: the config's)")
     ap.add_argument("--cluster", type=int, default=0, help="CTAs per problem (0: automatic)")
     ap.add_argument("--transform", default="split_bf16", choices=["split_bf16", "fp64"])
-    ap.add_argument("--ref-rotations", type=int, default=50000)
+    ap.add_argument("--ref-rotations", type=int, default=0, help="oracle rotation sample (0: 40000 at n <= 1024, 8000 above)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests of the stream to replay")
@@ -1122,12 +1194,13 @@ def main():
             run_batched_reference(args, ws, rank)
         else:
             run_batched_ours(args, ws, rank, local)
-    elif args.workload in ("p1", "svd", "hilbert"):
+    elif args.workload in ("p1", "svd", "hilbert", "multi"):
         if args.impl == "reference":
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable": "no reference arm for this extra workload"}))
         else:
-            {"p1": run_p1, "svd": run_svd, "hilbert": run_hilbert}[args.workload](args, ws, rank, local)
+            {"p1": run_p1, "svd": run_svd, "hilbert": run_hilbert, "multi": run_multi}[args.workload](
+                args, ws, rank, local)
     elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:

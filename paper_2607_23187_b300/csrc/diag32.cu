@@ -87,6 +87,28 @@ __device__ __forceinline__ void round_tile(int b, const float* __restrict__ A0, 
     if (!isA) b -= T * T;
     const int tr = b % T, tc = b / T;     // tile row (positions tr*32..), tile col
     const int tid = threadIdx.x;
+    // each thread: one 2x2 block (row pair a, col pair bb) of the tile.  Its
+    // entries do not depend on the rotations, so they are loaded first and
+    // their latency overlaps the rotations' computation below.
+    const int a = tid & 15, bb = tid >> 4;
+    const int rp = tr * 32 + 2 * a, cp = tc * 32 + 2 * bb;
+    const int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
+    float x00, x10, x01, x11;
+    if (isA) {
+        const int r0 = tour_sigma(rp, m), r1 = tour_sigma(rp + 1, m);
+        x00 = A0[r0 + (long long)c0 * npad];
+        x10 = A0[r1 + (long long)c0 * npad];
+        x01 = A0[r0 + (long long)c1 * npad];
+        x11 = A0[r1 + (long long)c1 * npad];
+    } else {
+        // Q rows are plain (no permutation); columns follow the positions.
+        // This thread's rows: tr*32 + a and tr*32 + a + 16.
+        const int r = tr * 32 + a;
+        x00 = Q0[r + (long long)c0 * npad];
+        x01 = Q0[r + (long long)c1 * npad];
+        x10 = Q0[r + 16 + (long long)c0 * npad];
+        x11 = Q0[r + 16 + (long long)c1 * npad];
+    }
     // rotation of the 16 pairs of this tile's columns (and rows, for A)
     if (tid < 32) {
         int which = tid >> 4, k = tid & 15;
@@ -101,16 +123,9 @@ __device__ __forceinline__ void round_tile(int b, const float* __restrict__ A0, 
         else { cs_r[k][0] = c; cs_r[k][1] = s; }
     }
     __syncthreads();
-    // each thread: one 2x2 block (row pair a, col pair bb) of the tile
-    const int a = tid & 15, bb = tid >> 4;
-    const int rp = tr * 32 + 2 * a, cp = tc * 32 + 2 * bb;
     const float cb = cs_c[bb][0], sb = cs_c[bb][1];
     if (isA) {
         const float ca = cs_r[a][0], sa = cs_r[a][1];
-        int r0 = tour_sigma(rp, m), r1 = tour_sigma(rp + 1, m);
-        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
-        float x00 = A0[r0 + (long long)c0 * npad], x10 = A0[r1 + (long long)c0 * npad];
-        float x01 = A0[r0 + (long long)c1 * npad], x11 = A0[r1 + (long long)c1 * npad];
         float z00, z01, z10, z11;
         rot2x2_sym(ca, sa, cb, sb, x00, x01, x10, x11, z00, z01, z10, z11);
         if (rp == cp && sa != 0.0f) { z01 = 0.0f; z10 = 0.0f; }
@@ -119,13 +134,11 @@ __device__ __forceinline__ void round_tile(int b, const float* __restrict__ A0, 
         A1[rp + (long long)(cp + 1) * npad] = z01;
         A1[rp + 1 + (long long)(cp + 1) * npad] = z11;
     } else {
-        // Q rows are plain (no permutation); columns follow the positions
-        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
-        for (int r = tr * 32 + a; r < tr * 32 + 32; r += 16) {
-            float q0 = Q0[r + (long long)c0 * npad], q1 = Q0[r + (long long)c1 * npad];
-            Q1[r + (long long)cp * npad] = q0 * cb + q1 * sb;
-            Q1[r + (long long)(cp + 1) * npad] = -q0 * sb + q1 * cb;
-        }
+        const int r = tr * 32 + a;
+        Q1[r + (long long)cp * npad] = x00 * cb + x01 * sb;
+        Q1[r + (long long)(cp + 1) * npad] = -x00 * sb + x01 * cb;
+        Q1[r + 16 + (long long)cp * npad] = x10 * cb + x11 * sb;
+        Q1[r + 16 + (long long)(cp + 1) * npad] = -x10 * sb + x11 * cb;
     }
     __syncthreads();
 }
@@ -235,6 +248,27 @@ __device__ __forceinline__ void refine_tile(int bt, const float* __restrict__ O0
     if (!isO) bt -= T * T;
     const int tr = bt % T, tc = bt / T;
     const int tid = threadIdx.x;
+    // this thread's 2x2 block (row pair a, col pair bb), loaded before the
+    // rotations are known (its entries do not depend on them)
+    const int a = tid & 15, bb = tid >> 4;
+    const int rp = tr * 32 + 2 * a, cp = tc * 32 + 2 * bb;
+    const int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
+    const int r0 = tour_sigma(rp, m), r1 = tour_sigma(rp + 1, m);
+    float x00 = 0.0f, x10 = 0.0f, x01 = 0.0f, x11 = 0.0f;
+    if (isO) {
+        if (rp != cp) {
+            x00 = O0[r0 + (long long)c0 * npad];
+            x10 = O0[r1 + (long long)c0 * npad];
+            x01 = O0[r0 + (long long)c1 * npad];
+            x11 = O0[r1 + (long long)c1 * npad];
+        }
+    } else {
+        const int r = tr * 32 + a;   // rows r and r + 16
+        x00 = D0[r + (long long)c0 * npad];
+        x01 = D0[r + (long long)c1 * npad];
+        x10 = D0[r + 16 + (long long)c0 * npad];
+        x11 = D0[r + 16 + (long long)c1 * npad];
+    }
     if (tid < 32) {
         int which = tid >> 4, k = tid & 15;
         int pairpos = (which == 0 ? tc : tr) * 32 + 2 * k;
@@ -262,13 +296,9 @@ __device__ __forceinline__ void refine_tile(int bt, const float* __restrict__ O0
         else pr_r[k] = r;
     }
     __syncthreads();
-    const int a = tid & 15, bb = tid >> 4;
-    const int rp = tr * 32 + 2 * a, cp = tc * 32 + 2 * bb;
     const RefPair pc = pr_c[bb];
     if (isO) {
         const RefPair pa = pr_r[a];
-        int r0 = tour_sigma(rp, m), r1 = tour_sigma(rp + 1, m);
-        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
         float z00, z01, z10, z11;
         if (rp == cp) {
             // diagonal block: its rotation moves b into the FP64 diagonal
@@ -281,8 +311,6 @@ __device__ __forceinline__ void refine_tile(int bt, const float* __restrict__ O0
                 pl1[rp + 1] = pl0[r1];
             }
         } else {
-            float x00 = O0[r0 + (long long)c0 * npad], x10 = O0[r1 + (long long)c0 * npad];
-            float x01 = O0[r0 + (long long)c1 * npad], x11 = O0[r1 + (long long)c1 * npad];
             rot2x2_sym(pa.c, pa.s, pc.c, pc.s, x00, x01, x10, x11, z00, z01, z10, z11);
         }
         O1[rp + (long long)cp * npad] = z00;
@@ -290,9 +318,9 @@ __device__ __forceinline__ void refine_tile(int bt, const float* __restrict__ O0
         O1[rp + (long long)(cp + 1) * npad] = z01;
         O1[rp + 1 + (long long)(cp + 1) * npad] = z11;
     } else {
-        int c0 = tour_sigma(cp, m), c1 = tour_sigma(cp + 1, m);
-        for (int r = tr * 32 + a; r < tr * 32 + 32; r += 16) {
-            float q0 = D0[r + (long long)c0 * npad], q1 = D0[r + (long long)c1 * npad];
+        for (int h = 0; h < 2; ++h) {
+            const int r = tr * 32 + a + 16 * h;
+            const float q0 = h ? x10 : x00, q1 = h ? x11 : x01;
             float v0 = q0 * pc.c + q1 * pc.s;
             float v1 = -q0 * pc.s + q1 * pc.c;
             if (r == pc.pp) { v0 += pc.cm1; v1 -= pc.s; }
