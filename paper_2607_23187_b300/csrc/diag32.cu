@@ -20,10 +20,11 @@
 // So a sweep streams the matrix through HBM nb-1 times instead of npad-1
 // times for the scalar parallel order, and the streamed work is dense.
 //
-// Storage: the off-diagonal part in FP32 (kept exactly symmetric: each
-// off-diagonal super-block is computed once and written with its
-// transpose), the diagonal in FP64 (so rotations inside clusters narrower
-// than FP32 resolution still see their true differences).  Two uses:
+// Storage: the off-diagonal part in FP32 (kept exactly symmetric), the
+// diagonal in FP64 (so rotations inside clusters narrower than FP32
+// resolution still see their true differences), both scaled by a power of
+// two that brings the largest entry into [1/2, 1) (the basis does not
+// depend on the scale).  Two uses:
 //   diag_fp32    the decomposition of fl32(A): the basis X starts at I and
 //                is Q0 at the end;
 //   refine_fp32  the same iteration on a nearly diagonal B = X^T fl32(A) X
@@ -46,17 +47,24 @@ constexpr int BJ_NT = 256;   // threads per CTA
 constexpr int BJ_LD = 68;    // row stride of the 64 x 64 GEMM operands in shared memory (float4 rows)
 constexpr int BJ_ZLD = 65;   // odd row stride where a tile is read along columns
 constexpr int BJ_TILE = 64 * BJ_LD;
-constexpr size_t BJ_SMEM = 4 * BJ_TILE * sizeof(float);   // phase 2: four operand tiles
+constexpr size_t BJ_SMEM = 6 * BJ_TILE * sizeof(float);   // phase 2: six operand tiles
+// entries below this (after scaling the largest to [1/2, 1)) are not rotated
+// away: far below the FP32 resolution of the matrix (and of the stopping
+// tests), and their squares would leave the normal range
+constexpr float BJ_TINY = 8.673617379884035e-19f;   // 2^-60
 
 __host__ __device__ inline long long bj_npad(int n) { return ((long long)(n + 63) / 64) * 64; }
 
-// workspace (floats): O[npad^2] | X[npad^2] | dg[npad] doubles | E[npairs][64*64] | acc[4] doubles | slots
+// workspace (floats): O[npad^2] | X[npad^2] | dg[npad] doubles |
+// G[2][npairs][64*64] (G = I + E, by round parity) | Ed[2][npairs][64]
+// (the diagonal of E) | acc[8] doubles | slots
 struct BjWs {
     float* O;
     float* X;
     double* dg;
-    float* E;
-    double* acc;
+    float* G;
+    float* Ed;
+    double* acc;   // [0..3] convergence sums (two slots), [4] max |entry| (bit pattern)
     int* slots;
 };
 
@@ -66,15 +74,16 @@ __host__ __device__ inline BjWs bj_ws(float* ws, int n) {
     w.O = ws;
     w.X = ws + nn;
     w.dg = reinterpret_cast<double*>(ws + 2 * nn);
-    w.E = ws + 2 * nn + 2 * npad;
-    w.acc = reinterpret_cast<double*>(w.E + npairs * 4096);
-    w.slots = reinterpret_cast<int*>(w.acc + 4);
+    w.G = ws + 2 * nn + 2 * npad;
+    w.Ed = w.G + 2 * npairs * 4096;
+    w.acc = reinterpret_cast<double*>(w.Ed + 2 * npairs * 64);
+    w.slots = reinterpret_cast<int*>(w.acc + 8);
     return w;
 }
 
 // Round-robin tournament (circle method) on N players, N even: in round r
 // pair 0 is (N-1, r) and pair k >= 1 is ((r+k) mod (N-1), (r-k) mod (N-1)).
-__device__ __forceinline__ void circle_pair(int r, int k, int N, int& p, int& q) {
+__host__ __device__ __forceinline__ void circle_pair(int r, int k, int N, int& p, int& q) {
     if (k == 0) {
         p = N - 1;
         q = r;
@@ -91,9 +100,10 @@ __device__ __forceinline__ int sup_idx(int t, int bi, int bj) { return t < 32 ? 
 
 // Z = G_a^T X G_b (G = [[c,-s],[s,c]]) for one 2x2 block, written as
 // Z[u][v] = (t(0,0) + t(1,1)) + (t(0,1) + t(1,0)) with
-// t(r,w) = (G_a[r][u] * G_b[w][v]) * X[r][w].  The block (b,a) is the
-// transpose formed from the same products summed in the same pairs, so a
-// matrix stays exactly symmetric through every rotation.
+// t(r,w) = (G_a[r][u] * G_b[w][v]) * X[r][w].  The block (b,a), computed
+// from X^T with the roles of a and b exchanged, forms the same products and
+// sums them in the same pairs, so it is exactly the transpose: a matrix
+// stays exactly symmetric through every rotation.
 __device__ __forceinline__ void rot2x2_sym(float ca, float sa, float cb, float sb, float x00, float x01,
                                            float x10, float x11, float& z00, float& z01, float& z10,
                                            float& z11) {
@@ -119,102 +129,190 @@ namespace {
 // ---------------------------------------------------------------------------
 // phase 1: one pair's diagonal super-block, inner sweeps in shared memory
 // ---------------------------------------------------------------------------
+// The diagonal is carried as an unevaluated sum hi + lo of two floats
+// (about 48 significant bits): the differences d_p - d_q that steer the
+// rotations stay accurate inside clusters far narrower than FP32 resolution,
+// and every step runs on the FP32 pipes.
+struct InnerSm {
+    float S[64 * BJ_ZLD];   // off-diagonal part, full symmetric storage (row u, col v)
+    float E[64 * BJ_ZLD];   // E = G - I
+    float dh[64], dl[64];   // diagonal, hi + lo
+    float4 prm[2][32];      // (c, s, c - 1, -) of the round's 32 rotations, by round parity
+    int pq[2][32];          // p | q << 8
+};
+static_assert(sizeof(InnerSm) <= BJ_SMEM, "phase-1 shared memory");
+
+// (h, l) += (ph, pl) for normalised float-float numbers (Knuth's TwoSum,
+// then Dekker's FastTwoSum to renormalise)
+__device__ __forceinline__ void ff_add(float& h, float& l, float ph, float pl) {
+    const float s = h + ph;
+    const float bb = s - h;
+    float e = (h - (s - bb)) + (ph - bb);
+    e = e + (l + pl);
+    const float nh = s + e;
+    l = e - (nh - s);
+    h = nh;
+}
+
+// Warp 0: the rotations of inner round `ir` (pair table row ir) into buffer
+// `buf`; the 2x2 diagonal blocks are finished here (t b moves into the
+// diagonal, the pair's off-diagonal entry becomes zero).
+__device__ __forceinline__ void inner_rotations(InnerSm& s, const unsigned short* __restrict__ ptab, int ir,
+                                                int buf) {
+    const int k = threadIdx.x;
+    const int pqv = ptab[ir * 32 + k];
+    const int p = pqv & 255, q = pqv >> 8;
+    const float b = s.S[p * BJ_ZLD + q];
+    float c = 1.0f, sn = 0.0f, cm1 = 0.0f;
+    if (fabsf(b) >= BJ_TINY) {
+        // d_p - d_q: the hi parts subtract exactly when they are close
+        const float d = (s.dh[p] - s.dh[q]) + (s.dl[p] - s.dl[q]);
+        // |d| < 2 and 2^-60 <= |b| < 1: no overflow, and 4 b^2 is normal
+        const float den = fabsf(d) + sqrtf(fmaf(d, d, 4.0f * (b * b)));
+        float t = __fdividef(2.0f * fabsf(b), den);
+        if (d != 0.0f && ((d < 0.0f) != (b < 0.0f))) t = -t;
+        c = rsqrtf(fmaf(t, t, 1.0f));
+        sn = t * c;
+        cm1 = __fdividef(-(t * t) * (c * c), 1.0f + c);   // c - 1 without cancellation
+        const float ph = t * b, pl = fmaf(t, b, -ph);      // t b exactly
+        ff_add(s.dh[p], s.dl[p], ph, pl);
+        ff_add(s.dh[q], s.dl[q], -ph, -pl);
+        s.S[p * BJ_ZLD + q] = 0.0f;
+        s.S[q * BJ_ZLD + p] = 0.0f;
+    }
+    s.prm[buf][k] = make_float4(c, sn, cm1, 0.0f);
+    s.pq[buf][k] = pqv;
+}
+
 __device__ void bj_inner(int k, int round, int nblk, long long npad, float* __restrict__ O,
-                         double* __restrict__ dg, float* __restrict__ Eg, int inner_sweeps, float* sm,
-                         const unsigned short* __restrict__ tri) {
-    float* Ss = sm;                      // off-diagonal part, 64 x 65 (row u, col v)
-    float* Es = Ss + 64 * BJ_ZLD;        // E = G - I, 64 x 65
-    double* dS = reinterpret_cast<double*>(Es + 64 * BJ_ZLD);   // FP64 diagonal
-    float* pc = reinterpret_cast<float*>(dS + 64);              // c[32] s[32] (c-1)[32]
-    int* pix = reinterpret_cast<int*>(pc + 96);                 // p[32] q[32]
-    const int tid = threadIdx.x;
+                         double* __restrict__ dg, float* __restrict__ Gg, float* __restrict__ Edg,
+                         int inner_sweeps, float* sm, const unsigned short* __restrict__ ptab) {
+    InnerSm& s = *reinterpret_cast<InnerSm*>(sm);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int bi, bj;
     circle_pair(round, k, nblk, bi, bj);
     for (int e = tid; e < 4096; e += BJ_NT) {
         const int u = e & 63, v = e >> 6;
-        Ss[u * BJ_ZLD + v] = O[sup_idx(u, bi, bj) + sup_idx(v, bi, bj) * npad];
-        Es[u * BJ_ZLD + v] = 0.0f;
+        s.S[u * BJ_ZLD + v] = __ldcg(O + sup_idx(u, bi, bj) + sup_idx(v, bi, bj) * npad);
+        s.E[u * BJ_ZLD + v] = 0.0f;
     }
-    if (tid < 64) dS[tid] = dg[sup_idx(tid, bi, bj)];
+    if (tid < 64) {
+        const double d = __ldcg(dg + sup_idx(tid, bi, bj));
+        const float h = (float)d;
+        s.dh[tid] = h;
+        s.dl[tid] = (float)(d - (double)h);
+    }
     __syncthreads();
-    for (int isw = 0; isw < inner_sweeps; ++isw) {
-        for (int ir = 0; ir < 63; ++ir) {
-            if (tid < 32) {
-                int p, q;
-                circle_pair(ir, tid, 64, p, q);
-                const float b = Ss[p * BJ_ZLD + q];
-                float c = 1.0f, s = 0.0f, cm1 = 0.0f;
-                if (b != 0.0f) {
-                    const double dd = dS[p] - dS[q];
-                    const float d = (float)dd;
-                    // hypotf neither overflows nor underflows: den >= 2|b| > 0
-                    const float den = fabsf(d) + hypotf(d, 2.0f * b);
-                    float t = 2.0f * fabsf(b) / den;
-                    if (dd != 0.0 && ((dd < 0.0) != (b < 0.0f))) t = -t;
-                    c = rsqrtf(1.0f + t * t);
-                    s = t * c;
-                    cm1 = -(t * t) * (c * c) / (1.0f + c);   // c - 1 without cancellation
-                    const double tb = (double)t * (double)b;
-                    dS[p] += tb;
-                    dS[q] -= tb;
-                    Ss[p * BJ_ZLD + q] = 0.0f;
-                    Ss[q * BJ_ZLD + p] = 0.0f;
-                }
-                pc[tid] = c;
-                pc[32 + tid] = s;
-                pc[64 + tid] = cm1;
-                pix[tid] = p;
-                pix[32 + tid] = q;
+    if (warp == 0) inner_rotations(s, ptab, 0, 0);
+    __syncthreads();
+    const int total = 63 * inner_sweeps;
+    for (int g = 0; g < total; ++g) {
+        const int buf = g & 1;
+        // off-diagonal 2x2 blocks: warp-uniform row pair u, lane = column
+        // pair v.  The blocks are disjoint, so all loads go first.
+        {
+            const int pqv = s.pq[buf][lane];
+            const int pv = pqv & 255, qv = pqv >> 8;
+            const float4 rv = s.prm[buf][lane];
+            int pu[4], qu[4];
+            float4 ru[4];
+            float x[4][4];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int pqu = s.pq[buf][warp + 8 * it];
+                pu[it] = pqu & 255;
+                qu[it] = pqu >> 8;
+                ru[it] = s.prm[buf][warp + 8 * it];
+                x[it][0] = s.S[pu[it] * BJ_ZLD + pv];
+                x[it][1] = s.S[pu[it] * BJ_ZLD + qv];
+                x[it][2] = s.S[qu[it] * BJ_ZLD + pv];
+                x[it][3] = s.S[qu[it] * BJ_ZLD + qv];
             }
-            __syncthreads();
-            // off-diagonal 2x2 blocks (pair u rows, pair v columns), u < v,
-            // written with their transposes
-            for (int w = tid; w < 496; w += BJ_NT) {
-                const int uv = tri[w];
-                const int u = uv & 255, v = uv >> 8;
-                const int pu = pix[u], qu = pix[32 + u], pv = pix[v], qv = pix[32 + v];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                if (warp + 8 * it == lane) continue;   // the pair's own block: done with its rotation
                 float z00, z01, z10, z11;
-                rot2x2_sym(pc[u], pc[32 + u], pc[v], pc[32 + v], Ss[pu * BJ_ZLD + pv], Ss[pu * BJ_ZLD + qv],
-                           Ss[qu * BJ_ZLD + pv], Ss[qu * BJ_ZLD + qv], z00, z01, z10, z11);
-                Ss[pu * BJ_ZLD + pv] = z00;
-                Ss[pu * BJ_ZLD + qv] = z01;
-                Ss[qu * BJ_ZLD + pv] = z10;
-                Ss[qu * BJ_ZLD + qv] = z11;
-                Ss[pv * BJ_ZLD + pu] = z00;
-                Ss[qv * BJ_ZLD + pu] = z01;
-                Ss[pv * BJ_ZLD + qu] = z10;
-                Ss[qv * BJ_ZLD + qu] = z11;
+                rot2x2_sym(ru[it].x, ru[it].y, rv.x, rv.y, x[it][0], x[it][1], x[it][2], x[it][3], z00, z01, z10,
+                           z11);
+                s.S[pu[it] * BJ_ZLD + pv] = z00;
+                s.S[pu[it] * BJ_ZLD + qv] = z01;
+                s.S[qu[it] * BJ_ZLD + pv] = z10;
+                s.S[qu[it] * BJ_ZLD + qv] = z11;
             }
-            // E <- E J + (J - I) on columns p, q of every row
-            for (int w = tid; w < 2048; w += BJ_NT) {
-                const int i = w & 63, kk = w >> 6;
-                const int p = pix[kk], q = pix[32 + kk];
-                const float c = pc[kk], s = pc[32 + kk], cm1 = pc[64 + kk];
-                const float e0 = Es[i * BJ_ZLD + p], e1 = Es[i * BJ_ZLD + q];
-                float v0 = e0 * c + e1 * s;
-                float v1 = -e0 * s + e1 * c;
-                if (i == p) { v0 += cm1; v1 -= s; }
-                if (i == q) { v0 += s; v1 += cm1; }
-                Es[i * BJ_ZLD + p] = v0;
-                Es[i * BJ_ZLD + q] = v1;
-            }
-            __syncthreads();
         }
+        __syncthreads();
+        if (warp == 0) {
+            if (g + 1 < total) inner_rotations(s, ptab, (g + 1) % 63, buf ^ 1);
+        } else {
+            // E <- E J + (J - I): rows lane and lane + 32 of the pairs
+            // warp-1, warp+6, ... (at most 5); loads first
+            float e0[5][2], e1[5][2];
+            int pp[5], qq[5];
+            float4 rr[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                const int kk = warp - 1 + 7 * j;
+                if (kk < 32) {
+                    const int pqv = s.pq[buf][kk];
+                    pp[j] = pqv & 255;
+                    qq[j] = pqv >> 8;
+                    rr[j] = s.prm[buf][kk];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        e0[j][h] = s.E[(lane + 32 * h) * BJ_ZLD + pp[j]];
+                        e1[j][h] = s.E[(lane + 32 * h) * BJ_ZLD + qq[j]];
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 5; ++j) {
+                if (warp - 1 + 7 * j >= 32) continue;
+                const float4 r = rr[j];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = lane + 32 * h;
+                    float v0 = e0[j][h] * r.x + e1[j][h] * r.y;
+                    float v1 = -e0[j][h] * r.y + e1[j][h] * r.x;
+                    if (i == pp[j]) { v0 += r.z; v1 -= r.y; }
+                    if (i == qq[j]) { v0 += r.y; v1 += r.z; }
+                    s.E[i * BJ_ZLD + pp[j]] = v0;
+                    s.E[i * BJ_ZLD + qq[j]] = v1;
+                }
+            }
+        }
+        __syncthreads();
     }
     for (int e = tid; e < 4096; e += BJ_NT) {
         const int u = e & 63, v = e >> 6;
-        O[sup_idx(u, bi, bj) + sup_idx(v, bi, bj) * npad] = Ss[u * BJ_ZLD + v];
-        const int r = e >> 6, cc = e & 63;   // E row-major, contiguous in cc
-        Eg[(long long)k * 4096 + r * 64 + cc] = Es[r * BJ_ZLD + cc];
+        __stcg(O + sup_idx(u, bi, bj) + sup_idx(v, bi, bj) * npad, s.S[u * BJ_ZLD + v]);
+        const int r = e >> 6, cc = e & 63;   // G row-major, contiguous in cc
+        const float ev = s.E[r * BJ_ZLD + cc];
+        __stcg(Gg + (long long)k * 4096 + r * 64 + cc, r == cc ? 1.0f + ev : ev);
     }
-    if (tid < 64) dg[sup_idx(tid, bi, bj)] = dS[tid];
+    if (tid < 64) {
+        dg[sup_idx(tid, bi, bj)] = (double)s.dh[tid] + (double)s.dl[tid];
+        __stcg(Edg + (long long)k * 64 + tid, s.E[tid * BJ_ZLD + tid]);
+    }
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // phase 2: dense 64 x 64 x 64 products in FP32
 // ---------------------------------------------------------------------------
-// acc[a][b] += sum_k L[k][4ty+a] R[k][4tx+b]; L and R k-major with row
+// Shared-memory tiles (64 x BJ_LD floats each): operand tiles L[2] and
+// R[2] double-buffered so that the next unit's copies run under the
+// current unit's products, G_P and T for the off-diagonal units.
+constexpr int BJ_L0 = 0, BJ_R0 = 2, BJ_GP = 4, BJ_T = 5;
+
+__device__ __forceinline__ void cp16(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// acc[a][b] = sum_k L[k][4ty+a] R[k][4tx+b]; L and R k-major with row
 // stride BJ_LD.  A warp reads two distinct L rows (broadcast) and one
 // 256-byte R row per k.
 __device__ __forceinline__ void mm64(const float* __restrict__ L, const float* __restrict__ R, float acc[4][4]) {
@@ -236,40 +334,25 @@ __device__ __forceinline__ void mm64(const float* __restrict__ L, const float* _
     }
 }
 
-// dst[k*BJ_LD + j] = E[k][j] + (k == j): G = I + E, row-major
-__device__ __forceinline__ void load_g(const float* __restrict__ E, float* dst) {
+// copies (in flight until the next wait) of G (row-major 64 x 64 in global)
+// to dst[k*BJ_LD + j]
+__device__ __forceinline__ void issue_g(const float* __restrict__ G, float* dst) {
     for (int f = threadIdx.x; f < 1024; f += BJ_NT) {
         const int k = f >> 4, j4 = (f & 15) * 4;
-        float4 v = *reinterpret_cast<const float4*>(E + k * 64 + j4);
-        if (k >= j4 && k < j4 + 4) {
-            if (k == j4) v.x += 1.0f;
-            else if (k == j4 + 1) v.y += 1.0f;
-            else if (k == j4 + 2) v.z += 1.0f;
-            else v.w += 1.0f;
-        }
-        *reinterpret_cast<float4*>(dst + k * BJ_LD + j4) = v;
+        cp16(dst + k * BJ_LD + j4, G + k * 64 + j4);
     }
 }
 
-// dst[v*BJ_LD + u] = M[row(u) + col(v)*npad]: a 64 x 64 tile, column-major;
+// copies of the 64 x 64 tile M[row(u) + col(v)*npad] to dst[v*BJ_LD + u];
 // rows are two runs of 32 (r0, r1) or one run of 64 (r1 = r0 + 32)
-__device__ __forceinline__ void load_tile(const float* __restrict__ M, long long npad, int r0, int r1, int c0,
-                                          int c1, float* dst) {
+__device__ __forceinline__ void issue_tile(const float* __restrict__ M, long long npad, int r0, int r1, int c0,
+                                           int c1, float* dst) {
     for (int f = threadIdx.x; f < 1024; f += BJ_NT) {
         const int v = f >> 4, u4 = (f & 15) * 4;
         const int gr = u4 < 32 ? r0 + u4 : r1 + u4 - 32;
         const int gc = v < 32 ? c0 + v : c1 + v - 32;
-        *reinterpret_cast<float4*>(dst + v * BJ_LD + u4) =
-            *reinterpret_cast<const float4*>(M + gr + (long long)gc * npad);
+        cp16(dst + v * BJ_LD + u4, M + gr + (long long)gc * npad);
     }
-}
-
-__device__ __forceinline__ void store_acc(float acc[4][4], float* dst, int ld) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) dst[(4 * ty + a) * ld + 4 * tx + b] = acc[a][b];
 }
 
 __device__ __forceinline__ void store_acc4(float acc[4][4], float* dst) {
@@ -280,135 +363,265 @@ __device__ __forceinline__ void store_acc4(float acc[4][4], float* dst) {
             make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
 }
 
-// off-diagonal super-block (kp, kq), kp < kq: S_PQ <- G_P^T S_PQ G_Q, and
-// its transpose into S_QP
-__device__ void bj_apply_off(int kp, int kq, int round, int nblk, long long npad, float* __restrict__ O,
-                             const float* __restrict__ Eg, float* sm) {
-    float* Lb = sm;                  // S_PQ (k-major), later Z (stride 65)
-    float* Rb = sm + BJ_TILE;        // G_Q
-    float* Tb = sm + 2 * BJ_TILE;    // T = S_PQ G_Q, row-major
-    float* Gb = sm + 3 * BJ_TILE;    // G_P
-    int pi, pj, qi, qj;
-    circle_pair(round, kp, nblk, pi, pj);
-    circle_pair(round, kq, nblk, qi, qj);
-    load_tile(O, npad, pi * 32, pj * 32, qi * 32, qj * 32, Lb);
-    load_g(Eg + (long long)kq * 4096, Rb);
-    load_g(Eg + (long long)kp * 4096, Gb);
-    __syncthreads();
-    float acc[4][4];
-    mm64(Lb, Rb, acc);               // T[i][j] = sum_k S[i][k] G_Q[k][j]
-    store_acc4(acc, Tb);
-    __syncthreads();
-    mm64(Gb, Tb, acc);               // Z[i][j] = sum_k G_P[k][i] T[k][j]
-    store_acc(acc, Lb, BJ_ZLD);
-    __syncthreads();
-    for (int e = threadIdx.x; e < 4096; e += BJ_NT) {
-        const int i = e & 63, j = e >> 6;
-        O[sup_idx(i, pi, pj) + sup_idx(j, qi, qj) * npad] = Lb[i * BJ_ZLD + j];
-        const int i2 = e >> 6, j2 = e & 63;
-        O[sup_idx(j2, qi, qj) + sup_idx(i2, pi, pj) * npad] = Lb[i2 * BJ_ZLD + j2];
-    }
-    __syncthreads();
+// [lo, hi): part `part` of `parts` equal contiguous shares of `count` units
+__device__ __forceinline__ void unit_range(long long count, int part, int parts, long long& lo, long long& hi) {
+    lo = count * part / parts;
+    hi = count * (part + 1) / parts;
 }
 
-// basis rows [64 rt, 64 rt + 64) on the columns of pair k: X <- X G_k, plus
-// E_k on the pair's own rows when the basis is carried as D = X - I
-__device__ void bj_apply_basis(int rt, int k, int round, int nblk, long long npad, float* __restrict__ X,
-                               const float* __restrict__ Eg, int delta, float* sm) {
-    float* Lb = sm;
-    float* Rb = sm + BJ_TILE;
-    float* Zb = sm + 2 * BJ_TILE;    // stride 65
-    int bi, bj;
-    circle_pair(round, k, nblk, bi, bj);
-    const int r0 = rt * 64;
-    load_tile(X, npad, r0, r0 + 32, bi * 32, bj * 32, Lb);
-    const float* Ek = Eg + (long long)k * 4096;
-    load_g(Ek, Rb);
-    __syncthreads();
-    float acc[4][4];
-    mm64(Lb, Rb, acc);
-    store_acc(acc, Zb, BJ_ZLD);
-    __syncthreads();
-    for (int e = threadIdx.x; e < 4096; e += BJ_NT) {
-        const int i = e & 63, j = e >> 6;
-        const int g = r0 + i;
-        float z = Zb[i * BJ_ZLD + j];
-        if (delta) {
-            const int blk = g >> 5;
-            if (blk == bi) z += Ek[(g - bi * 32) * 64 + j];
-            else if (blk == bj) z += Ek[(32 + g - bj * 32) * 64 + j];
+// pair indices of off-diagonal unit u (kp < kq, kp-major order)
+__device__ __forceinline__ void off_unit(long long u, int npairs, int& kp, int& kq) {
+    kp = 0;
+    long long rem = u;
+    while (rem >= npairs - 1 - kp) {
+        rem -= npairs - 1 - kp;
+        ++kp;
+    }
+    kq = kp + 1 + (int)rem;
+}
+
+// Off-diagonal units [lo, hi) of round `round`: S_PQ <- G_P^T S_PQ G_Q,
+// written to S_PQ and, transposed, to S_QP.  Consecutive units share kp, so
+// G_P is copied once per change of kp; the next unit's S_PQ and G_Q are
+// copied during the current unit's products.
+__device__ void run_off_units(long long lo, long long hi, int npairs, int round, int nblk, long long npad,
+                              float* __restrict__ O, const float* __restrict__ Gg, float* sm) {
+    if (lo >= hi) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float* Gp = sm + BJ_GP * BJ_TILE;
+    float* Tb = sm + BJ_T * BJ_TILE;
+    int kp, kq;
+    off_unit(lo, npairs, kp, kq);
+    {
+        int pi, pj, qi, qj;
+        circle_pair(round, kp, nblk, pi, pj);
+        circle_pair(round, kq, nblk, qi, qj);
+        issue_tile(O, npad, pi * 32, pj * 32, qi * 32, qj * 32, sm + BJ_L0 * BJ_TILE);
+        issue_g(Gg + (long long)kq * 4096, sm + BJ_R0 * BJ_TILE);
+        issue_g(Gg + (long long)kp * 4096, Gp);
+        cp_commit();
+    }
+    int b = 0;
+    for (long long u = lo; u < hi; ++u, b ^= 1) {
+        int kp1 = kp, kq1 = kq;
+        const bool more = u + 1 < hi;
+        if (more) {
+            off_unit(u + 1, npairs, kp1, kq1);
+            int pi, pj, qi, qj;
+            circle_pair(round, kp1, nblk, pi, pj);
+            circle_pair(round, kq1, nblk, qi, qj);
+            issue_tile(O, npad, pi * 32, pj * 32, qi * 32, qj * 32, sm + (BJ_L0 + (b ^ 1)) * BJ_TILE);
+            issue_g(Gg + (long long)kq1 * 4096, sm + (BJ_R0 + (b ^ 1)) * BJ_TILE);
+            cp_commit();
+            cp_wait_prev();
+        } else {
+            cp_wait_all();
         }
-        X[g + (long long)sup_idx(j, bi, bj) * npad] = z;
+        __syncthreads();
+        float acc[4][4];
+        mm64(sm + (BJ_L0 + b) * BJ_TILE, sm + (BJ_R0 + b) * BJ_TILE, acc);   // T = S_PQ G_Q
+        store_acc4(acc, Tb);
+        __syncthreads();
+        mm64(Gp, Tb, acc);                                                    // Z = G_P^T T
+        int pi, pj, qi, qj;
+        circle_pair(round, kp, nblk, pi, pj);
+        circle_pair(round, kq, nblk, qi, qj);
+        // Z[i][j], i = 4ty + a (P side), j = 4tx + b (Q side): four
+        // consecutive rows of a column, and four consecutive columns of a
+        // row of the transpose, are 16-byte stores
+        const int rP = sup_idx(4 * ty, pi, pj), rQ = sup_idx(4 * tx, qi, qj);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            *reinterpret_cast<float4*>(O + rP + (long long)(rQ + c) * npad) =
+                make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+            *reinterpret_cast<float4*>(O + rQ + (long long)(rP + c) * npad) =
+                make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+        }
+        if (more && kp1 != kp) {
+            __syncthreads();   // everyone is done with G_P
+            issue_g(Gg + (long long)kp1 * 4096, Gp);
+            cp_commit();
+            cp_wait_all();
+        }
+        kp = kp1;
+        kq = kq1;
     }
     __syncthreads();
 }
 
-// The whole iteration in one cooperative launch; the phases and rounds are
-// separated by grid-wide barriers and the convergence test after each sweep
-// is taken by every CTA from the same global sums.
+// Basis units of round `round` (G of that round in Gg, E's diagonal in
+// Edg): unit v is the 64 rows [64 (v % nrt), +64) of the columns of pair
+// v / nrt, X <- X G, plus E = G - I on the pair's own rows when the basis is
+// carried as D = X - I.  Units are taken one at a time from the queue
+// counter *xq (zero at the start of the step), one unit ahead so that its
+// copies run under the current unit's product; CTAs that finish their inner
+// solve early take more.
+__device__ void run_basis_queue(int* xq, long long nX, long long nrt, int round, int nblk, long long npad,
+                                float* __restrict__ X, const float* __restrict__ Gg, const float* __restrict__ Edg,
+                                int delta, float* sm, long long* s_next) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (threadIdx.x == 0) *s_next = atomicAdd(xq, 1);
+    __syncthreads();
+    long long v = *s_next;
+    __syncthreads();
+    auto issue = [&](long long unit, int buf) {
+        const int k = (int)(unit / nrt), r0 = (int)(unit % nrt) * 64;
+        int bi, bj;
+        circle_pair(round, k, nblk, bi, bj);
+        issue_tile(X, npad, r0, r0 + 32, bi * 32, bj * 32, sm + (BJ_L0 + buf) * BJ_TILE);
+        issue_g(Gg + (long long)k * 4096, sm + (BJ_R0 + buf) * BJ_TILE);
+        cp_commit();
+    };
+    if (v < nX) issue(v, 0);
+    int b = 0;
+    while (v < nX) {
+        if (threadIdx.x == 0) *s_next = atomicAdd(xq, 1);
+        __syncthreads();
+        const long long vn = *s_next;
+        if (vn < nX) {
+            issue(vn, b ^ 1);
+            cp_wait_prev();
+        } else {
+            cp_wait_all();
+        }
+        __syncthreads();
+        const float* Rb = sm + (BJ_R0 + b) * BJ_TILE;
+        float acc[4][4];
+        mm64(sm + (BJ_L0 + b) * BJ_TILE, Rb, acc);
+        const int k = (int)(v / nrt), r0 = (int)(v % nrt) * 64;
+        int bi, bj;
+        circle_pair(round, k, nblk, bi, bj);
+        const int g0 = r0 + 4 * ty;   // this thread's four rows
+        if (delta) {
+            const int blk = g0 >> 5;
+            if (blk == bi || blk == bj) {
+                const int t0 = blk == bi ? g0 - bi * 32 : 32 + g0 - bj * 32;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int t = t0 + a, j = 4 * tx + c;
+                        acc[a][c] += t == j ? __ldcg(Edg + (long long)k * 64 + t) : Rb[t * BJ_LD + j];
+                    }
+            }
+        }
+        const int cQ = sup_idx(4 * tx, bi, bj);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<float4*>(X + g0 + (long long)(cQ + c) * npad) =
+                make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        __syncthreads();   // L[b], R[b] and s_next free again
+        v = vn;
+        b ^= 1;
+    }
+}
+
+// The whole iteration in one cooperative launch.  Per round r:
+//   step 1  inner solves of round r (one CTA per pair) and the basis update
+//           of round r - 1 (it only needs E of that round, kept in the other
+//           parity buffer), taken from a queue by every CTA once its inner
+//           solve, if any, is done;
+//   step 2  the off-diagonal super-blocks of round r on every CTA;
+// grid-wide barriers between the steps.  The basis update of the last round
+// runs once the iteration stops.  The convergence test after each sweep is
+// taken by every CTA from the same global sums.
 //   delta = 0: S = fl32(A) (its diagonal too), basis X = I;  out = X
 //   delta = 1: S = B with the FP64 diagonal, D = 0;           out = D
-__global__ void __launch_bounds__(BJ_NT) bjac32_coop_kernel(const double* __restrict__ A, long long lda, int n,
-                                                            float* ws, float* __restrict__ out, int max_sweeps,
-                                                            int inner_sweeps, int delta, double stop_tol,
-                                                            int slot) {
+// acc[4] must be zero at launch (the scale's maximum is reduced into it).
+__global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __restrict__ A, long long lda, int n,
+                                                               float* ws, float* __restrict__ out, int max_sweeps,
+                                                               int inner_sweeps, int delta, double stop_tol,
+                                                               int slot) {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ __align__(16) float sm[];
-    __shared__ unsigned short tri[496];
+    __shared__ unsigned short ptab[63 * 32];
     __shared__ double s_off[BJ_NT / 32], s_all[BJ_NT / 32];
+    __shared__ long long s_chunk;
     const long long npad = bj_npad(n), nn = npad * npad;
     const BjWs w = bj_ws(ws, n);
+    int* xq = w.slots + 2;   // basis-unit queue of the current step 1
     const int nblk = (int)(npad / 32), npairs = nblk / 2;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int t = threadIdx.x; t < 496; t += BJ_NT) {
-        int u = 0, rem = t;
-        while (rem >= 31 - u) { rem -= 31 - u; ++u; }
-        tri[t] = (unsigned short)(u | ((u + 1 + rem) << 8));
+    for (int t = threadIdx.x; t < 63 * 32; t += BJ_NT) {
+        int p, q;
+        circle_pair(t >> 5, t & 31, 64, p, q);
+        ptab[t] = (unsigned short)(p | (q << 8));
     }
+    // scale 2^-e with max |A| * 2^-e in [1/2, 1)
+    {
+        double mx = 0.0;
+        for (long long e = gtid; e < (long long)n * n; e += gstride) {
+            const int r = (int)(e % n), c = (int)(e / n);
+            mx = fmax(mx, fabs(A[r + (long long)c * lda]));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) s_off[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < BJ_NT / 32; ++k) mx = fmax(mx, s_off[k]);
+            atomicMax(reinterpret_cast<unsigned long long*>(w.acc + 4), (unsigned long long)__double_as_longlong(mx));
+        }
+    }
+    grid.sync();
+    int ex = 0;
+    {
+        const double mx = __ldcg(w.acc + 4);
+        if (mx > 0.0) frexp(mx, &ex);
+        ex = max(ex, -1000);   // keep 2^-ex finite for matrices of subnormal numbers
+    }
+    const double scale = ldexp(1.0, -ex);
     for (long long e = gtid; e < nn; e += gstride) {
         const int r = (int)(e % npad), c = (int)(e / npad);
-        w.O[e] = (r != c && r < n && c < n) ? (float)A[r + (long long)c * lda] : 0.0f;
+        w.O[e] = (r != c && r < n && c < n) ? (float)(A[r + (long long)c * lda] * scale) : 0.0f;
         w.X[e] = (!delta && r == c) ? 1.0f : 0.0f;
     }
     for (long long p = gtid; p < npad; p += gstride) {
         double d = 0.0;
         if (p < n) {
-            d = A[p + p * lda];
+            d = A[p + p * lda] * scale;
             if (!delta) d = (double)(float)d;
         }
         w.dg[p] = d;
     }
     if (gtid < 4) w.acc[gtid] = 0.0;
+    if (gtid == 0) *xq = 0;
     grid.sync();
-    const int nA = npairs * (npairs - 1) / 2;
-    const int nunits = nA + (int)(npad / 64) * npairs;
+    const long long nA = (long long)npairs * (npairs - 1) / 2;
+    const long long nrt = npad / 64;
+    const long long nX = nrt * npairs;
+    long long ax_lo, ax_hi;
+    unit_range(nA, blockIdx.x, gridDim.x, ax_lo, ax_hi);
+    const long long gbuf = (long long)npairs * 4096, ebuf = (long long)npairs * 64;
+    long long gr = 0;          // rounds done (all sweeps): parity of the G buffers
+    int pend_round = -1;       // round whose basis update is pending
     double prev = -1.0;
     int done = max_sweeps;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        for (int r = 0; r < nblk - 1; ++r) {
+        for (int r = 0; r < nblk - 1; ++r, ++gr) {
+            float* Gr = w.G + (gr & 1) * gbuf;
+            float* Er = w.Ed + (gr & 1) * ebuf;
             for (int k = blockIdx.x; k < npairs; k += gridDim.x)
-                bj_inner(k, r, nblk, npad, w.O, w.dg, w.E, inner_sweeps, sm, tri);
+                bj_inner(k, r, nblk, npad, w.O, w.dg, Gr, Er, inner_sweeps, sm, ptab);
+            if (pend_round >= 0)
+                run_basis_queue(xq, nX, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                                w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
             grid.sync();
-            for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-                if (u < nA) {
-                    int kp = 0, rem = u;
-                    while (rem >= npairs - 1 - kp) { rem -= npairs - 1 - kp; ++kp; }
-                    bj_apply_off(kp, kp + 1 + rem, r, nblk, npad, w.O, w.E, sm);
-                } else {
-                    const int v = u - nA;
-                    bj_apply_basis(v / npairs, v % npairs, r, nblk, npad, w.X, w.E, delta, sm);
-                }
-            }
+            if (gtid == 0) *xq = 0;   // nobody takes from the queue until the next step 1
+            run_off_units(ax_lo, ax_hi, npairs, r, nblk, npad, w.O, Gr, sm);
+            pend_round = r;
             grid.sync();
         }
         // off(S)^2 and ||S||_F^2
         double off = 0.0, all = 0.0;
         for (long long e = gtid; e < nn; e += gstride) {
-            const double v = (double)w.O[e];
+            const double v = (double)__ldcg(w.O + e);
             off += v * v;
         }
-        for (long long p = gtid; p < npad; p += gstride) all += w.dg[p] * w.dg[p];
+        for (long long p = gtid; p < npad; p += gstride) {
+            const double d = __ldcg(w.dg + p);
+            all += d * d;
+        }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             all += __shfl_xor_sync(0xffffffffu, all, o);
@@ -446,13 +659,18 @@ __global__ void __launch_bounds__(BJ_NT) bjac32_coop_kernel(const double* __rest
         }
         grid.sync();   // the other slot is zero before anyone adds to it
     }
+    // the last round's basis update
+    if (pend_round >= 0)
+        run_basis_queue(xq, nX, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                        w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
+    grid.sync();
     if (blockIdx.x == 0 && threadIdx.x == 0) w.slots[slot] = done;
     // indices never move, so the basis is in the original column order;
     // the padding columns are unit vectors of padding rows and are dropped
     const long long tot = (long long)n * n;
     for (long long e = gtid; e < tot; e += gstride) {
         const int r = (int)(e % n), c = (int)(e / n);
-        out[e] = w.X[r + (long long)c * npad];
+        out[e] = __ldcg(w.X + r + (long long)c * npad);
     }
 }
 
@@ -469,10 +687,13 @@ cudaError_t bj_launch(const double* A, long long lda, int n, float* out, float* 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bjac32_coop_kernel, BJ_NT, BJ_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const BjWs w = bj_ws(ws, n);
+    e = cudaMemsetAsync(w.acc, 0, 8 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
     const long long npad = bj_npad(n);
     const long long npairs = npad / 64;
-    const long long units = npairs * (npairs - 1) / 2 + (npad / 64) * npairs;
-    int grid = (int)std::min<long long>((long long)sms * std::min(per_sm, 3), std::max<long long>(units, 1));
+    const long long units = std::max(npairs * (npairs - 1) / 2, npairs + (npad / 64) * npairs);
+    int grid = (int)std::min<long long>((long long)sms * std::min(per_sm, 2), units);
     if (max_grid > 0 && grid > max_grid) grid = max_grid;   // share the GPU (all CTAs must be co-resident)
     int inner = bj_inner_sweeps();
     void* args[] = {(void*)&A,      (void*)&lda,   (void*)&n,        (void*)&ws,   (void*)&out,
@@ -485,7 +706,7 @@ cudaError_t bj_launch(const double* A, long long lda, int n, float* out, float* 
 
 size_t diag_fp32_ws_floats(int n) {
     const long long npad = bj_npad(n), npairs = npad / 64;
-    return (size_t)(2 * npad * npad + 2 * npad + npairs * 4096 + 8 + 16);
+    return (size_t)(2 * npad * npad + 2 * npad + 2 * npairs * (4096 + 64) + 16 + 16);   // ... acc[8] | slots[3]
 }
 
 // Q0 <- eigenvectors of fl32(A) (n x n, ld n).  ws: diag_fp32_ws_floats(n)
