@@ -196,6 +196,7 @@ struct SolveWs {
     DevInfo* info; // 1
     double* Z;     // n x n (refinement)
     unsigned long long* maxsum;   // 1 (refinement)
+    int* K;        // n x n screening keys of the Jacobi iteration
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -204,15 +205,15 @@ static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     size_t nn = (size_t)n * n;
     h->last_n = n;
     const size_t nz = h->opts.refine_steps > 0 ? nn * 8 : 8;
-    size_t sz[12] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
-                     diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo), nz, 8};
+    size_t sz[13] = {nn * 8, nn * 8, nn * 8, nn * 8, (size_t)n * 8, nn * 4,
+                     diag_fp32_ws_floats(n) * 4, (size_t)n * 4, 16, sizeof(DevInfo), nz, 8, nn * 4};
     size_t tot = 0;
     for (size_t s : sz) tot += align256(s);
     int r = h->ws.ensure(tot, st);
     if (r) return r;
     char* p = static_cast<char*>(h->ws.p);
-    void* ptrs[12];
-    for (int k = 0; k < 12; ++k) {
+    void* ptrs[13];
+    for (int k = 0; k < 13; ++k) {
         ptrs[k] = p;
         p += align256(sz[k]);
     }
@@ -228,6 +229,7 @@ static int layout_ws(pjac_handle* h, int n, SolveWs* w, cudaStream_t st) {
     w->info = (DevInfo*)ptrs[9];
     w->Z = (double*)ptrs[10];
     w->maxsum = (unsigned long long*)ptrs[11];
+    w->K = (int*)ptrs[12];
     return PJAC_OK;
 }
 
@@ -458,8 +460,10 @@ static long long budget_ns(const pjac_opts& o) {
 }
 
 static int run_jacobi(pjac_handle* h, double* A1, long long lda1, int n, double* Vw, long long ldvw,
-                      pjac_pivot pivot, double tol, double* Wd, DevInfo* dinfo, cudaStream_t st) {
+                      pjac_pivot pivot, double tol, double* Wd, DevInfo* dinfo, int* K, cudaStream_t st) {
     JacArgs a;
+    a.K = K;
+    a.ldk = n;
     a.A = A1;
     a.lda = lda1;
     a.V = Vw;
@@ -557,7 +561,7 @@ static int solve_pipeline(pjac_handle* h, const double* A, int n, int lda, pjac_
         r = precondition_ws(h, A, n, lda, nullptr, w.Vw, n, w.A1, n, w, st);
         if (r) return r;
     }
-    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, w.K, st);
     if (r) return r;
     CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
     if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16 && !h->opts.no_precondition)
@@ -630,7 +634,7 @@ extern "C" int pjac_solve_preconditioned(pjac_handle* h, double* A1, int n, int 
         CK(set_identity(w.Vw, n, n, st));
     }
     CK(cudaEventRecord(h->ev[2], st));
-    r = run_jacobi(h, A1, lda1, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    r = run_jacobi(h, A1, lda1, n, w.Vw, n, pivot, tol, w.Wd, w.info, w.K, st);
     if (r) return r;
     CK(launch_readout(w.Wd, w.Vw, n, n, W, V, ldv, w.rank, st));
     CK(cudaEventRecord(h->ev[3], st));
@@ -707,7 +711,7 @@ extern "C" int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, 
         if (r) return r;
     }
     CK(cudaEventRecord(h->ev[2], st));
-    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, st);
+    r = run_jacobi(h, w.A1, n, n, w.Vw, n, pivot, tol, w.Wd, w.info, w.K, st);
     if (r) return r;
     // the rotated matrix B V, its column norms, the sorted factors
     r = product_mnk(h, false, false, m, n, n, 1.0, B, ldb, w.Vw, n, 0.0, BF, m, st);

@@ -34,6 +34,8 @@ struct JacArgs {
     long long budget_ns;
     DevInfo* info;
     unsigned long long seed;   // PJAC_PIVOT_RANDOM
+    int* K = nullptr;      // optional: screening key of every entry (n x n, ld ldk), kept current
+    long long ldk = 0;
 };
 
 // One problem of the batched form, as the device sees it.  All matrices

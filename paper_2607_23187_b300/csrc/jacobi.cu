@@ -80,14 +80,18 @@ struct Sh {
     int pi, pj, nresc, decision;
     int win, pad4;          // inbox index of the pending pivot
     int key_eps, pad2;
+#ifdef PJAC_PROFILE
+    long long t_top;
+#endif
 };
 
-// warps 3 and up finish (c, s) of the 3 candidates of each of up to 16 ranks
-static_assert((NT / 32 - 3) * 32 >= 48, "too few warps for the cosines of the published candidates");
+// warps 5 and up finish (c, s) of the 3 candidates of each of up to 16 ranks
+static_assert((NT / 32 - 5) * 32 >= 48, "too few warps for the cosines of the published candidates");
 
 #ifdef PJAC_PROFILE
 // Profiling build only: per-phase clock totals of CTA 0 and event counts.
 __device__ unsigned long long g_prof[40];
+__device__ unsigned long long g_rank[32];   // per cluster rank: loop top to arrive, arrive to wait done
 #define PROF_ADD(k, v) atomicAdd(&g_prof[k], (unsigned long long)(v))
 // exact evaluations made by this CTA (one counter per CTA)
 __device__ __forceinline__ unsigned int& prof_exact() {
@@ -322,7 +326,9 @@ __device__ Cand warp_select(Cand c, int pivot, const double* diag, Cand* wb) {
         const int pmin = __reduce_min_sync(0xffffffffu, pid);
         const int pmax = __reduce_max_sync(0xffffffffu, cont ? pid : -1);
         if (pmin == pmax) {
-            src = __ffs(__ballot_sync(0xffffffffu, cont && c.row < c.col)) - 1;
+            // one pair, possibly seen from both rows: the row < col view
+            const unsigned lo = __ballot_sync(0xffffffffu, cont && c.row < c.col);
+            src = __ffs(lo ? lo : b) - 1;
         } else {
             double v = -2.0;
             if (cont) {
@@ -398,26 +404,6 @@ __device__ void cta_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const doubl
     kA[0] = a1; kA[1] = a2; kB[0] = b1; kB[1] = b2;
 }
 
-// Best candidate over the first `width` lanes of a warp (width a power of
-// two <= 32; butterfly, every lane of the group ends with the maximum).  The
-// row and column travel packed in one word, with the candidate's exact
-// score (when known) and its origin tag (pad).
-__device__ __forceinline__ Cand warp_best(Cand c, int width, int pivot, const double* diag) {
-    for (int off = width >> 1; off > 0; off >>= 1) {
-        Cand o;
-        o.key = __shfl_xor_sync(0xffffffffu, c.key, off);
-        int rc = __shfl_xor_sync(0xffffffffu, (c.row << 16) | (c.col & 0xffff), off);
-        o.row = rc >> 16;
-        o.col = rc & 0xffff;
-        o.pad = __shfl_xor_sync(0xffffffffu, c.pad, off);
-        o.x = __shfl_xor_sync(0xffffffffu, c.x, off);
-        o.ex = __shfl_xor_sync(0xffffffffu, c.ex, off);
-        if (o.key == KEY_NONE) { o.row = -1; o.col = -1; }
-        if (better(o, c, pivot, diag)) c = o;
-    }
-    return c;
-}
-
 __device__ __forceinline__ double block_sum(double v, Sh& sh) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -470,9 +456,14 @@ __device__ __forceinline__ const Slot* peer_slot(Sh& sh, int par, int r) {
 
 // Rescan row k (block-wide): its best entry over l != k, in sec its second
 // entry, and in F the key bound of its remaining entries (from its third).
-__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& sec, int& F) {
+__device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& sec, int& F,
+                           bool store_keys = false) {
     const double* row = a.A + (long long)k * a.lda;
+    int* krow = (store_keys && a.K) ? a.K + (long long)k * a.ldk : nullptr;
     double dk = diag[k];
+#ifdef PJAC_PROFILE
+    const long long t_r0 = clock64();
+#endif
     Cand t1 = no_cand(), t2 = no_cand(), t3 = no_cand();
     for (int l0 = threadIdx.x; l0 < a.n; l0 += 4 * NT) {
         double xs[4];
@@ -488,12 +479,26 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, 
             Cand c;
             c.row = k; c.col = l; c.pad = 0; c.x = xs[u]; c.ex = -1.0;
             c.key = entry_key(a.pivot, xs[u], a.pivot == PJAC_PIVOT_GREEDY ? 0.0 : __dadd_rn(dk, -diag[l]));
-            if (better(c, t1, a.pivot, diag)) { t3 = t2; t2 = t1; t1 = c; }
-            else if (better(c, t2, a.pivot, diag)) { t3 = t2; t2 = c; }
-            else if (better(c, t3, a.pivot, diag)) t3 = c;
+            if (krow) __stcg(krow + l, c.key);
+            // most entries fail against the third at once
+            if (better(c, t3, a.pivot, diag)) {
+                if (better(c, t2, a.pivot, diag)) {
+                    t3 = t2;
+                    if (better(c, t1, a.pivot, diag)) { t2 = t1; t1 = c; }
+                    else t2 = c;
+                } else {
+                    t3 = c;
+                }
+            }
         }
     }
+#ifdef PJAC_PROFILE
+    const long long t_s0 = clock64();
+#endif
     Cand b = block_select(t1, a.pivot, diag, sh);
+#ifdef PJAC_PROFILE
+    const long long t_s1 = clock64();
+#endif
     const bool w1 = t1.key != KEY_NONE && t1.col == b.col;
     Cand offer = w1 ? t2 : t1;
     sec = block_select(offer, a.pivot, diag, sh);
@@ -503,10 +508,88 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, 
     if (o3.key != KEY_NONE && (o3.col == b.col || o3.col == sec.col)) o3 = t3;
     Cand third = block_select(o3, a.pivot, diag, sh);
     F = bound_from_exact(third, a.pivot);
+#ifdef PJAC_PROFILE
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        PROF_ADD(20, t_s0 - t_r0);
+        PROF_ADD(21, t_s1 - t_s0);
+        PROF_ADD(22, clock64() - t_s1);
+        PROF_ADD(23, 1);
+    }
+#endif
     return b;
 }
 
 // off(A)^2 * 2^-2e over the owned rows, e = ilogb(||A1||_F) (as the oracle).
+// Row rescan from the stored keys (column k of K holds the keys of row k):
+// each thread keeps the four largest keys of its columns; the head b is the
+// exact maximum among the entries within the tie band of the largest key,
+// sec the exact best of the listed entries other than b, and F the largest
+// listed key other than b's and sec's (an entry left out of a thread's list
+// has a key no larger than that thread's smallest listed key).  Returns
+// false, with nothing written, when some thread's list is full of
+// contenders for the maximum: then only the full rescan is exact.
+__device__ bool rescan_row_keys(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& b, Cand& sec,
+                                int& F) {
+    const int* kr = a.K + (long long)k * a.ldk;
+    const double* row = a.A + (long long)k * a.lda;
+    int lk[4] = {KEY_NONE, KEY_NONE, KEY_NONE, KEY_NONE}, lc[4] = {-1, -1, -1, -1};
+    constexpr int CH = 16;
+    for (int l0 = threadIdx.x; l0 < a.n; l0 += CH * NT) {
+        int ks[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int l = l0 + u * NT;
+            ks[u] = (l < a.n && l != k) ? __ldcg(kr + l) : KEY_NONE;
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            int kk = ks[u], cc = l0 + u * NT;
+            if (kk <= lk[3]) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (kk > lk[q]) {
+                    const int tk = lk[q], tc = lc[q];
+                    lk[q] = kk; lc[q] = cc;
+                    kk = tk; cc = tc;
+                }
+        }
+    }
+    const int kmax = block_max_int(lk[0], sh);
+    if (kmax == KEY_NONE) {
+        b = no_cand(); sec = no_cand(); F = KEY_NONE;
+        return true;
+    }
+    const bool gap = a.pivot != PJAC_PIVOT_GREEDY;
+    const bool exact_all = gap && kmax < KEY_SUB;
+    const int tie = gap ? KEY_GAP_TIE : 0;
+    const bool ovf = lk[3] != KEY_NONE && (exact_all || (long long)lk[3] >= (long long)kmax - tie);
+    if (__syncthreads_or(ovf)) return false;
+    Cand e[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        e[q] = no_cand();
+        if (lk[q] != KEY_NONE) {
+            e[q].key = lk[q]; e[q].row = k; e[q].col = lc[q]; e[q].x = ldcg(row + lc[q]);
+        }
+    }
+    Cand m = no_cand();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (better(e[q], m, a.pivot, diag)) m = e[q];
+    b = block_select(m, a.pivot, diag, sh);
+    Cand m2 = no_cand();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (e[q].col != b.col && better(e[q], m2, a.pivot, diag)) m2 = e[q];
+    sec = block_select(m2, a.pivot, diag, sh);
+    int r = KEY_NONE;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (lc[q] >= 0 && lc[q] != b.col && lc[q] != sec.col) r = max(r, lk[q]);
+    F = block_max_int(r, sh);
+    return true;
+}
+
 __device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, Sh& sh) {
     // eight independent partial sums over eight rows at a time: the loads of
     // a block overlap and no FMA waits on the previous one
@@ -679,6 +762,11 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 stcg(Ai + i, dii_new);
                 stcg(Aj + i, 0.0);
                 stcg(Ai + j, 0.0);
+                if (score && a.K) {
+                    const int kz = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO;
+                    __stcg(a.K + (long long)j * a.ldk + i, kz);
+                    __stcg(a.K + (long long)i * a.ldk + j, kz);
+                }
                 if (score) {
                     Cand z; z.key = (pivot == PJAC_PIVOT_GREEDY) ? 0 : KEY_ZERO; z.row = j; z.col = i;
                     z.pad = 0; z.x = 0.0; z.ex = -1.0;
@@ -719,6 +807,12 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 ky = gap_key(yn, __dadd_rn(dk, -dj));
             }
             if (r == 0) SLAP(6);
+            if (a.K) {
+                __stcg(a.K + (long long)i * a.ldk + k, kx);
+                __stcg(a.K + (long long)k * a.ldk + i, kx);
+                __stcg(a.K + (long long)j * a.ldk + k, ky);
+                __stcg(a.K + (long long)k * a.ldk + j, ky);
+            }
             Cand ci; ci.key = kx; ci.row = i; ci.col = k; ci.pad = 0; ci.x = xn; ci.ex = -1.0;
             Cand cj; cj.key = ky; cj.row = j; cj.col = k; cj.pad = 0; cj.x = yn; cj.ex = -1.0;
             if (better(ci, pI, pivot, diag)) pI = ci;
@@ -831,9 +925,10 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         for (int k = k0; k < k1; ++k) {
             Cand s2;
             int F;
-            Cand b = rescan_row(a, k, diag, sh, s2, F);
+            Cand b = rescan_row(a, k, diag, sh, s2, F, true);
             if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; cachef[k - k0] = F; }
         }
+        if (CLUSTER && a.K) cta_exchange_sync<CLUSTER>();   // every row's keys are stored
         __syncthreads();
         // The pending pivot, the same in every thread after publish_select:
         // pdec (0 rotate, 1 converged, 2 time budget, 3 rotation budget),
@@ -845,7 +940,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         // evaluated by three lanes at once, from one shared denominator --
         // push them into every rank's inbox, and select after the cluster
         // barrier.  The cosines and sines are not on the path to the
-        // decision: after the barrier, while warp 0 decides, warps 3 and up
+        // decision: after the barrier, while warp 0 decides, warps 5 and 6
         // finish them for every published candidate.  Every CTA ends with
         // the same winner in sh.sel and its rotation in pend_c, pend_s and
         // sh.t; the owners of rows i and j take those rows' new bests.
@@ -890,6 +985,10 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 }
             }
             SLAP(1);
+#ifdef PJAC_PROFILE
+            const long long t_arr = clock64();
+            if (tid == 0 && i >= 0 && rank < 16) atomicAdd(&g_rank[rank], (unsigned long long)(t_arr - sh.t_top));
+#endif
             if (CLUSTER) asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
             if (vupd && a.V) {
                 double* Vi = a.V + (long long)i * a.ldv;
@@ -907,9 +1006,14 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             if (CLUSTER) asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
             else __syncthreads();
             LAP(5);
+#ifdef PJAC_PROFILE
+            const long long t_wait = clock64();
+            if (tid == 0 && i >= 0 && rank < 16) atomicAdd(&g_rank[16 + rank], (unsigned long long)(t_wait - t_arr));
+#define WLAP(k) do { if (rank == 0 && lane == 0) PROF_ADD(32 + (k), clock64() - t_wait); } while (0)
+#else
+#define WLAP(k) ((void)0)
+#endif
             const int warp = tid >> 5, lane = tid & 31;
-            int width = 1;
-            while (width < P) width <<= 1;
             if (warp == 0) {
                 // the winner over all 3P published candidates, and the
                 // decision on it, broadcast through shared memory
@@ -921,9 +1025,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     c.pad = e;
                     if (better(c, g, pivot, diag)) g = c;
                 }
-                int w3 = 1;
-                while (w3 < 3 * P && w3 < 32) w3 <<= 1;
-                g = warp_best(g, w3, pivot, diag);
+                WLAP(4);
+                g = warp_select(g, pivot, diag, nullptr);
+                WLAP(5);
                 if (lane == 0) {
                     double v = -1.0;
                     int dec = 0;
@@ -957,6 +1061,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     }
                     sh.nresc = 0;
                 }
+                WLAP(0);
             } else if (i >= 0 && (warp == 1 || warp == 2)) {
                 // new heads of rows i and j and their bounds F; the owning
                 // CTA writes them into its cache
@@ -969,7 +1074,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     ka = (warp == 1) ? sl.ki[0] : sl.kj[0];
                     kb = (warp == 1) ? sl.ki[1] : sl.kj[1];
                 }
-                c = warp_best(c, width, pivot, diag);
+                c = warp_select(c, pivot, diag, nullptr);
                 warp_top2_keys(ka, kb);
                 const int row = (warp == 1) ? i : j;
                 if (lane == 0 && row >= k0 && row < k1) {
@@ -977,16 +1082,22 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     cache2[row - k0] = no_cand();
                     cachef[row - k0] = bound_without_head(c, ka, kb);
                 }
-            } else if (warp >= 3) {
+                if (warp == 1) WLAP(1);
+            } else if (warp >= 5) {
                 // cosine and sine of every published candidate's rotation
-                const int e = (warp - 3) * 32 + lane;
+                // (warps 5 and 6: not on warp 0's scheduler, whose FP64
+                // pipe the decision needs)
+                const int e = (warp - 5) * 32 + lane;
                 if (e < 3 * P) {
                     const double* pr = sh.inbox[par][e / 3].prm[e % 3];
                     rot_cs(pr[0], pr[1], pr[2], sh.cs[e][0], sh.cs[e][1]);
                 }
+                if (warp == 5) WLAP(2);
             }
             par ^= 1;
             __syncthreads();
+            if (warp == 0) WLAP(3);
+#undef WLAP
             pdec = sh.decision;
             ppi = sh.pi;
             ppj = sh.pj;
@@ -1014,6 +1125,9 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         bool stop_now = false;
         for (;;) {
             LAP(7);
+#ifdef PJAC_PROFILE
+            sh.t_top = clock64();
+#endif
             if (pdec == 2) { status = PJAC_ETIMEOUT; break; }
             if (pdec == 0) preload(ppi, ppj);   // the loads do not depend on the test below
             if (rot % ce == 0) {
@@ -1043,13 +1157,19 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             // rescans of owned rows whose best was in column i or j
             const int nr = sh.nresc;
             if (tid == 0) PROF_ADD(9, nr);
+#ifdef PJAC_PROFILE
+            const long long t_rs = clock64();
+#endif
             for (int r = 0; r < nr; ++r) {
                 int k = resc[r];
-                Cand s2;
+                Cand s2, b;
                 int F;
-                Cand b = rescan_row(a, k, diag, sh, s2, F);
+                if (!(a.K && rescan_row_keys(a, k, diag, sh, b, s2, F))) b = rescan_row(a, k, diag, sh, s2, F);
                 if (tid == 0) { cache[k - k0] = b; cache2[k - k0] = s2; cachef[k - k0] = F; }
             }
+#ifdef PJAC_PROFILE
+            if (rank == 0 && tid == 0 && nr > 0) { PROF_ADD(38, nr); PROF_ADD(39, clock64() - t_rs); }
+#endif
             __syncthreads();
             LAP(3);
             if (tid == 0)
@@ -1357,6 +1477,14 @@ extern "C" int pjac_prof_read(unsigned long long* out, int reset) {
     if (reset) {
         unsigned long long z[40] = {0};
         cudaMemcpyToSymbol(g_prof, z, sizeof(z));
+    }
+    return 0;
+}
+extern "C" int pjac_prof_rank_read(unsigned long long* out, int reset) {
+    cudaMemcpyFromSymbol(out, g_rank, sizeof(unsigned long long) * 32);
+    if (reset) {
+        unsigned long long z[32] = {0};
+        cudaMemcpyToSymbol(g_rank, z, sizeof(z));
     }
     return 0;
 }
