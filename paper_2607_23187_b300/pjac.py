@@ -182,6 +182,13 @@ class Handle:
         o = default_opts(**opts)
         _check(load().pjac_set_opts(self.h, ctypes.byref(o)))
 
+    def fp32_sweeps_done(self):
+        """(sweeps of the FP32 diagonalisation, sweeps of its refinement) made
+        by the handle's last low-precision eigenbasis (pjac_fp32_sweeps_done)."""
+        d, r = ctypes.c_int(), ctypes.c_int()
+        _check(load().pjac_fp32_sweeps_done(self.h, ctypes.byref(d), ctypes.byref(r)))
+        return d.value, r.value
+
     def close(self):
         if self.h:
             load().pjac_destroy(self.h)
