@@ -5,10 +5,11 @@ One step = one full solve of the workload through the hot path:
 FP32 diagonalisation -> Newton--Schulz -> A1 = Q^T A Q -> Jacobi (gap rule,
 off-diagonal stop at 1e-15 ||A1||_F) -> readout of W and V, with the input
 resident in HBM.  Workloads (synthetic, seeded; see pjac_inputs):
-  cfg2 (default): n = 1024, 32 clusters of 32 (spread 1e-8)
-  cfg3:           n = 4096, half the spectrum geometric 1..1e-6, half in 64
-                  clusters of 32 (spread 1e-10); --with-4096 adds one timed
-                  cfg3 solve to a cfg2 run
+  cfg3 (default): n = 4096, half the spectrum geometric 1..1e-6, half in 64
+                  clusters of 32 (spread 1e-10)
+  cfg2:           n = 1024, 32 clusters of 32 (spread 1e-8)
+  p1, svd, hilbert, multi, product: the paper's Sec. 4.1 example, the SVD
+                  forms, the multi-pivot variant and the split product
   batched:        10,000 problems, n log-uniform in [16, 256] (one step = the
                   whole batch)
   serve:          Poisson stream at 2000 req/s of n in {64..2048} (one step =
@@ -60,11 +61,17 @@ FP64_PEAK_TFLOPS = 1.199
 FP64_PEAK_SOURCE = "measured by pjac_probe_fp64 on a B300 of this pool (1.199 TFLOP/s; nominal 1.25)"
 
 # DRAM bytes (read + write) of one launch of the Jacobi kernel, from the
-# committed ncu capture (profiles/jacobi_single_kernel_cfg2_n1024.md); the
-# working set (A1 and V, 8 MB each at n = 1024) stays in L2, so the traffic
-# of a launch does not grow with its rotations.
-JACOBI_TRAFFIC_PER_LAUNCH = {}
-JACOBI_TRAFFIC_SOURCE = "no ncu capture of the current kernel at this order"
+# committed ncu captures, as (one-time bytes, bytes per rotation):
+#   n = 4096: an 8,000-rotation launch moved 6.93 GB; 0.19 GB of it is the
+#             initial scan (A1 read, key matrix written), the rest grows with
+#             the rotations (profiles/jacobi_single_kernel_cfg3_n4096.md);
+#   n = 1024: the working set stays in L2, 19.8 MB for a 30,000-rotation
+#             launch (profiles/jacobi_single_kernel_cfg2_n1024.md).
+JACOBI_DRAM = {4096: (0.19e9, (6.93e9 - 0.19e9) / 8000.0), 1024: (19.8e6, 0.0)}
+JACOBI_TRAFFIC_SOURCE = {
+    4096: "ncu dram__bytes_read+write of an 8,000-rotation launch, scaled by rotations (one-time 0.19 GB "
+          "+ 0.84 MB per rotation)",
+    1024: "ncu dram__bytes_read+write of a 30,000-rotation launch (working set in L2)"}
 
 
 class Clocks:
@@ -380,21 +387,23 @@ def run_ours(args, ws, rank, local):
 
     # roofline of the dominant kernel (the Jacobi kernel): FP64 arithmetic
     # against this GPU's measured FP64 rate; DRAM traffic per launch from the
-    # committed ncu capture (the working set, A1 and V, stays in L2)
+    # committed ncu captures (scaled by the rotations at n = 4096, where the
+    # working set does not fit in L2)
     inf = infos[-1]
     rot = inf["rotations"]
     jac_ms = float(np.median([i["ms_jacobi"] for i in infos]))
-    flops = 14.0 * n * rot     # per rotation: rows (2 mul + 2 fma), V (same), 2 key differences
+    flops = 18.0 * n * rot     # per rotation and owned index: rows i, j (8), V (8), 2 key differences
     achieved = flops / (jac_ms / 1000.0) / 1e12
     peaks = measured_peaks()
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": achieved / fp64_peak,
-            "traffic": JACOBI_TRAFFIC_PER_LAUNCH.get(n),
-            "traffic_source": JACOBI_TRAFFIC_SOURCE,
+            "traffic": (JACOBI_DRAM[n][0] + JACOBI_DRAM[n][1] * rot) if n in JACOBI_DRAM else None,
+            "traffic_source": JACOBI_TRAFFIC_SOURCE.get(n, "no ncu capture of the current kernel at this order"),
+            "algorithmic_bytes": 100.0 * n * rot,
             "kernel": "jacobi_single_kernel (one cluster of CTAs, one problem)",
             "peak_source": "measured in this run by pjac_probe_fp64 (FP64 FMA chains on every SM)",
             "ns_per_rotation": 1e6 * jac_ms / max(rot, 1),
-            "hbm_gbs_equiv": 80.0 * n * rot / (jac_ms / 1000.0) / 1e9,
+            "hbm_gbs_equiv": 100.0 * n * rot / (jac_ms / 1000.0) / 1e9,
             "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peaks["source"]}
 
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -667,11 +676,11 @@ def run_batched_ours(args, ws, rank, local):
     one_rate = len(sample) / t_one
     hp.close()
 
-    flops = float(np.sum(14.0 * ns * rot))
+    flops = float(np.sum(18.0 * ns * rot))
     achieved = flops / (ms / 1000.0) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "whole batched pipeline (6 kernels in one CUDA graph; the Jacobi kernel dominates)",
+            "kernel": "whole batched pipeline (6 kernels in one CUDA graph; stage shares under \"stages\")",
             "peak_source": FP64_PEAK_SOURCE,
             "us_per_rotation_per_cta": 1e3 * ms * 2 * 148 / max(rot.sum(), 1)}
     out = {"metric": BATCHED_METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -739,7 +748,8 @@ def serving_config(count):
     return {"workload": "serving: the first %d requests of the seeded Poisson stream (2000 req/s, seed 2), "
                         "n in {64,128,256,512,1024,2048} with p = {.3,.25,.2,.12,.08,.05}, clustered spectra "
                         "(n/8 clusters, spread 1e-8), 4 distinct matrices per size; gap rule, off-diagonal "
-                        "stop 1e-15, eigenvalues and vectors, host buffers in and out" % count,
+                        "stop 1e-15, eigenvalues and vectors, host buffers in and out; the server's solves take "
+                        "the first-order refinement steps (--refine; micro-batches one more)" % count,
             "requests": count, "rate_per_s": 2000.0,
             "l2": "each request's matrix is uploaded from host memory when admitted",
             "parallelism": "single GPU: micro-batched n <= 256, one cluster per larger request; 32 lanes "
@@ -812,7 +822,7 @@ def run_serving(args, ws, rank, local):
     count = args.requests
     t_arr, sidx, pool = pin.serving_workload(count=count)
     sizes = pin.SERVE_SIZES
-    srv = pjac.Server(max_slots=32)
+    srv = pjac.Server(max_slots=32, refine_steps=args.refine, fp32_sweeps=args.fp32_sweeps)
 
     def serve(reqs, arrivals, record=True):
         """Submit reqs at their arrival offsets, poll until all finish."""
@@ -898,6 +908,10 @@ def run_serving(args, ws, rank, local):
                           "p99": float(np.percentile(lat_ms[sel], 99))}
                     for cls, sel in (("n<=256", small_sel), ("n>256", ~small_sel)) if sel.any()},
                 "per_size_count": {str(m): int(np.sum(sidx == k)) for k, m in enumerate(sizes)},
+                "latency_ms_by_size": {
+                    str(m): {"p50": float(np.percentile(lat_ms[sidx == k], 50)),
+                             "p99": float(np.percentile(lat_ms[sidx == k], 99))}
+                    for k, m in enumerate(sizes) if np.any(sidx == k)},
                 "accuracy": {"max_rel_eig_err": worst, "ok_1e-13": worst <= 1e-13, "all_status_ok": ok},
                 "one_at_a_time_fp64": {"solves_per_s": count / (fin - t_arr[0]),
                                        "p50_ms": float(np.percentile(lat1, 50)),
