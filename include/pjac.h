@@ -428,8 +428,11 @@ int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
 
 /* Number of kernel launches of this library that one pjac_solve of size n
  * makes with the handle's current options (preconditioner products,
- * element-wise steps, the Jacobi kernel, the readout).  A diagnostic for
- * launch accounting; returns -1 when h is NULL or n is out of range. */
+ * element-wise steps, the Jacobi kernel, the readout).  With refine_steps
+ * > 0 the Newton--Schulz steps of each refinement step depend on the size
+ * of its correction: the count is that of the handle's last solve of order
+ * n, or an upper bound before there is one.  A diagnostic for launch
+ * accounting; returns -1 when h is NULL or n is out of range. */
 int pjac_solve_launch_count(pjac_handle* h, int n);
 
 /* Number of kernel launches of this library that one pjac_product of shape

@@ -315,7 +315,22 @@ def transform_exact(a: np.ndarray, q: np.ndarray) -> np.ndarray:
 
 REFINE_TAU = 0.01          # pairs with |a_ij| > tau |a_jj - a_ii| are left to Jacobi
 REFINE_MAX_ROWSUM = 0.25   # max_i sum_j |D_ij| (>= ||D||_2) is scaled down to at most this
-REFINE_NS_STEPS = 5
+REFINE_NS_STEPS = 5         # at most; fewer when ||D||_2 is small (refine_ns_count)
+
+
+def refine_ns_count(rho: float) -> int:
+    """Newton--Schulz steps that take Z = I + D (D antisymmetric, ||D||_2 <=
+    rho <= 1/4) to orthogonality: the defect R = Z^T Z - I = D^T D starts at
+    ||R|| <= rho^2 and one step maps r to 3/4 r^2 + 1/4 r^3 <= r^2, so k steps
+    leave at most rho^(2^(k+1)); the count is the least k >= 1 with
+    rho^(2^(k+1)) <= 2^-56, at most REFINE_NS_STEPS."""
+    if rho <= 0.0:
+        return 0
+    bits = -np.log2(rho)                 # rho = 2^-bits, bits >= 2
+    k = 1
+    while k < REFINE_NS_STEPS and (2.0 ** (k + 1)) * bits < 56.0:
+        k += 1
+    return k
 
 
 def refine_step(a1: np.ndarray, q: np.ndarray, tau: float = REFINE_TAU) -> Tuple[np.ndarray, np.ndarray]:
@@ -327,8 +342,8 @@ def refine_step(a1: np.ndarray, q: np.ndarray, tau: float = REFINE_TAU) -> Tuple
     with |e_ij| > tau |d_j - d_i| (near-degenerate) get D_ij = 0 and are left
     to the Jacobi iteration.  D is scaled so that its largest absolute row
     sum (an upper bound of ||D||_2 for antisymmetric D) is at most 1/4, Z is
-    I + D made orthogonal by Newton--Schulz (5 steps from
-    ||Z^T Z - I||_2 = ||D||_2^2 <= 1/16, which leaves an error near 1e-21),
+    I + D made orthogonal by Newton--Schulz (refine_ns_count(||D||) steps:
+    4 from ||Z^T Z - I||_2 = ||D||_2^2 <= 1/16, fewer for a small D),
     and the pair becomes (Z^T A1 Z symmetrised, Q Z) -- an exact orthogonal
     similarity up to rounding, so the spectrum is unchanged."""
     a1 = np.asarray(a1, dtype=np.float64)
@@ -340,9 +355,11 @@ def refine_step(a1: np.ndarray, q: np.ndarray, tau: float = REFINE_TAU) -> Tuple
         dm = np.where(keep, e / np.where(keep, delta, 1.0), 0.0)
     np.fill_diagonal(dm, 0.0)
     nrm = np.max(np.sum(np.abs(dm), axis=1))
+    if nrm == 0.0:
+        return a1, np.asarray(q, dtype=np.float64)   # nothing to refine
     if nrm > REFINE_MAX_ROWSUM:
         dm = dm * (REFINE_MAX_ROWSUM / nrm)
-    z = reorth_ns(np.eye(a1.shape[0]) + dm, REFINE_NS_STEPS)
+    z = reorth_ns(np.eye(a1.shape[0]) + dm, refine_ns_count(min(nrm, REFINE_MAX_ROWSUM)))
     a2 = z.T @ (a1 @ z)
     return 0.5 * (a2 + a2.T), np.asarray(q, dtype=np.float64) @ z
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -66,6 +68,9 @@ struct pjac_handle {
     DevBuf svdws;       // SVD: the m x n rotated matrix
     int coop_cap = 0;   // cap of the cooperative grids (0: the whole GPU)
     int last_n = 0;     // order of the last workspace layout
+    // refinement steps of the last solve: order, steps applied, their
+    // Newton--Schulz steps in all (for pjac_solve_launch_count)
+    int ref_n = 0, ref_done = 0, ref_ns = 0;
     cudaEvent_t ev[4];
     std::mutex mu;
 };
@@ -333,12 +338,36 @@ static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, 
 // product's error is relative to |E| rather than to |Z| ~ 1:
 //   R = E^T E + E + E^T,  E <- E - R/2 - E R/2              (Newton--Schulz)
 //   T = A1 E,  A1 <- A1 + (T + T^T + E^T T),  Q <- Q + Q E.
+// Newton--Schulz steps that make Z = I + E orthogonal (E antisymmetric,
+// ||E||_2 <= rho <= 1/4, bounded by its largest absolute row sum): the defect
+// Z^T Z - I = E^T E starts at most rho^2 and a step maps r to
+// 3/4 r^2 + 1/4 r^3 <= r^2, so k steps leave rho^(2^(k+1)); the least k >= 1
+// with rho^(2^(k+1)) <= 2^-56, at most REFINE_NS_STEPS.
+static int refine_ns_count(double rho) {
+    if (!(rho > 0.0)) return 0;
+    const double bits = -std::log2(rho);
+    int k = 1;
+    while (k < REFINE_NS_STEPS && std::ldexp(1.0, k + 1) * bits < 56.0) ++k;
+    return k;
+}
+
 static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, long long ldq, int n, SolveWs& w,
                        cudaStream_t st) {
     double* E = w.Z;
     CK(refine_build(A1, lda1, n, REFINE_TAU, E, w.maxsum, REFINE_MAX_ROWSUM, st));
+    // the largest absolute row sum of D before scaling: the step count of
+    // the orthogonalisation (one small copy; the solve is not captured)
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, w.maxsum, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double rowsum = 0.0;
+    std::memcpy(&rowsum, &bits, sizeof(rowsum));
+    const int ns = refine_ns_count(std::min(rowsum, REFINE_MAX_ROWSUM));
+    if (ns == 0) return PJAC_OK;   // D = 0: nothing to refine
+    h->ref_done++;
+    h->ref_ns += ns;
     int r;
-    for (int it = 0; it < REFINE_NS_STEPS; ++it) {
+    for (int it = 0; it < ns; ++it) {
         r = product(h, true, false, n, 1.0, E, n, E, n, 0.0, w.Y, n, st);         // Y = E^T E
         if (r) return r;
         CK(refine_r(w.Y, E, n, st));                                               // R = Y + E + E^T
@@ -382,6 +411,8 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
     r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
     if (r) return r;
     CK(symmetrize(A1, lda1, n, st));
+    h->ref_n = n;
+    h->ref_done = h->ref_ns = 0;
     for (int k = 0; k < h->opts.refine_steps; ++k) {
         r = refine_step(h, A1, lda1, Q, ldq, n, w, st);
         if (r) return r;
@@ -706,6 +737,8 @@ extern "C" int pjac_svd(pjac_handle* h, const double* B, int m, int n, int ldb, 
     r = product_mnk(h, true, false, n, n, m, 1.0, BF, m, BF, m, 0.0, w.A1, n, st);
     if (r) return r;
     CK(symmetrize(w.A1, n, n, st));
+    h->ref_n = n;
+    h->ref_done = h->ref_ns = 0;
     for (int k = 0; k < h->opts.refine_steps; ++k) {
         r = refine_step(h, w.A1, n, w.Vw, n, n, w, st);
         if (r) return r;
@@ -793,10 +826,20 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
     // transform (two products) and symmetrise, Jacobi, readout (two kernels)
     c += 2 * P + 1 + 1 + 2;
-    // refinement steps: build and scale, Newton--Schulz (two products and
+    // refinement steps: build and scale (every step), then for the steps
+    // with a nonzero correction its Newton--Schulz steps (two products and
     // two element-wise steps each), three products, the A1 update,
-    // symmetrise, the Q update
-    c += h->opts.refine_steps * (2 + REFINE_NS_STEPS * (2 * P + 2) + 3 * P + 3);
+    // symmetrise, the Q update.  The Newton--Schulz count depends on the
+    // correction's size: the handle's last solve of this order gives it,
+    // else the largest count is assumed.
+    if (h->opts.refine_steps > 0) {
+        int done = h->opts.refine_steps, nss = h->opts.refine_steps * REFINE_NS_STEPS;
+        if (h->ref_n == n) {
+            done = h->ref_done;
+            nss = h->ref_ns;
+        }
+        c += 2 * h->opts.refine_steps + nss * (2 * P + 2) + done * (3 * P + 3);
+    }
     if (split) c += 1;  // product status folded into the solve record
     return c;
 }

@@ -454,3 +454,24 @@ def test_multi_pivot_step_brute_force():
         oracle.rotate(ref, i, j)
     assert m["steps"] == 1 and m["rotations"] == len(piv) >= 2
     assert np.array_equal(m["a"], ref)
+
+
+def test_refine_ns_count_reaches_orthogonality():
+    """The refinement's Newton--Schulz count: from Z = I + D with D
+    antisymmetric and ||D||_2 <= rho, refine_ns_count(rho) steps leave Z
+    orthogonal to rounding (the defect bound rho^(2^(k+1)) <= 2^-56), and the
+    count falls as D shrinks (4 at the largest correction, 1 for tiny ones)."""
+    rng = np.random.default_rng(17)
+    n = 60
+    counts = []
+    for rho in (0.25, 1e-2, 1e-4, 1e-9):
+        g = rng.standard_normal((n, n))
+        d = g - g.T
+        d *= rho / np.max(np.sum(np.abs(d), axis=1))      # row-sum bound = rho >= ||D||_2
+        k = oracle.refine_ns_count(rho)
+        counts.append(k)
+        z = oracle.reorth_ns(np.eye(n) + d, k)
+        assert np.linalg.norm(z.T @ z - np.eye(n), 2) <= 4e-15, (rho, k)
+    assert counts == sorted(counts, reverse=True)
+    assert counts[0] == 4 and counts[-1] == 1
+    assert oracle.refine_ns_count(0.0) == 0
