@@ -4,7 +4,7 @@
 // eigensolver to use; here it is a blocked parallel-order two-sided Jacobi
 // method in FP32.
 //
-// The order-npad matrix (npad = n rounded up to 64; the padding rows and
+// The order-npad matrix (npad = n rounded up to 128; the padding rows and
 // columns are zero, so every rotation that touches them is the identity and
 // they never mix with the real indices) is cut into nb = npad/32 blocks of
 // 32 indices.  A sweep is the nb-1 rounds of the round-robin tournament over
@@ -47,22 +47,24 @@ constexpr int BJ_NT = 256;   // threads per CTA
 constexpr int BJ_LD = 68;    // row stride of the 64 x 64 GEMM operands in shared memory (float4 rows)
 constexpr int BJ_ZLD = 65;   // odd row stride where a tile is read along columns
 constexpr int BJ_TILE = 64 * BJ_LD;
-constexpr size_t BJ_SMEM = 6 * BJ_TILE * sizeof(float);   // phase 2: six operand tiles
+constexpr size_t BJ_SMEM = 6 * BJ_TILE * sizeof(float);   // phase 2: six operand tiles (104,448 B)
 // entries below this (after scaling the largest to [1/2, 1)) are not rotated
 // away: far below the FP32 resolution of the matrix (and of the stopping
 // tests), and their squares would leave the normal range
 constexpr float BJ_TINY = 8.673617379884035e-19f;   // 2^-60
 
-__host__ __device__ inline long long bj_npad(int n) { return ((long long)(n + 63) / 64) * 64; }
+__host__ __device__ inline long long bj_npad(int n) { return ((long long)(n + 127) / 128) * 128; }
 
 // workspace (floats): O[npad^2] | X[npad^2] | dg[npad] doubles |
-// G[2][npairs][64*64] (G = I + E, by round parity) | Ed[2][npairs][64]
-// (the diagonal of E) | acc[8] doubles | slots
+// G[2][npairs][64*64] (G = I + E row-major, by round parity) |
+// Gc[2][npairs][64*64] (the same G column-major) | Ed[2][npairs][64] (the
+// diagonal of E) | acc[8] doubles | slots
 struct BjWs {
     float* O;
     float* X;
     double* dg;
     float* G;
+    float* Gc;
     float* Ed;
     double* acc;   // [0..3] convergence sums (two slots), [4] max |entry| (bit pattern)
     int* slots;
@@ -75,7 +77,8 @@ __host__ __device__ inline BjWs bj_ws(float* ws, int n) {
     w.X = ws + nn;
     w.dg = reinterpret_cast<double*>(ws + 2 * nn);
     w.G = ws + 2 * nn + 2 * npad;
-    w.Ed = w.G + 2 * npairs * 4096;
+    w.Gc = w.G + 2 * npairs * 4096;
+    w.Ed = w.Gc + 2 * npairs * 4096;
     w.acc = reinterpret_cast<double*>(w.Ed + 2 * npairs * 64);
     w.slots = reinterpret_cast<int*>(w.acc + 8);
     return w;
@@ -185,8 +188,9 @@ __device__ __forceinline__ void inner_rotations(InnerSm& s, const unsigned short
 }
 
 __device__ void bj_inner(int k, int round, int nblk, long long npad, float* __restrict__ O,
-                         double* __restrict__ dg, float* __restrict__ Gg, float* __restrict__ Edg,
-                         int inner_sweeps, float* sm, const unsigned short* __restrict__ ptab) {
+                         double* __restrict__ dg, float* __restrict__ Gg, float* __restrict__ Gcg,
+                         float* __restrict__ Edg, int inner_sweeps, float* sm,
+                         const unsigned short* __restrict__ ptab) {
     InnerSm& s = *reinterpret_cast<InnerSm*>(sm);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int bi, bj;
@@ -288,6 +292,8 @@ __device__ void bj_inner(int k, int round, int nblk, long long npad, float* __re
         const int r = e >> 6, cc = e & 63;   // G row-major, contiguous in cc
         const float ev = s.E[r * BJ_ZLD + cc];
         __stcg(Gg + (long long)k * 4096 + r * 64 + cc, r == cc ? 1.0f + ev : ev);
+        const float et = s.E[cc * BJ_ZLD + r];   // column-major: element (cc, r) at [r][cc]
+        __stcg(Gcg + (long long)k * 4096 + r * 64 + cc, r == cc ? 1.0f + et : et);
     }
     if (tid < 64) {
         dg[sup_idx(tid, bi, bj)] = (double)s.dh[tid] + (double)s.dl[tid];
@@ -449,14 +455,16 @@ __device__ void run_off_units(long long lo, long long hi, int npairs, int round,
     __syncthreads();
 }
 
-// Basis units of round `round` (G of that round in Gg, E's diagonal in
+// Basis units on the FP32 pipes (the refinement pass, whose products must
+// keep FP32 accuracy relative to the correction D): round `round` (G of
+// that round in Gg, E's diagonal in
 // Edg): unit v is the 64 rows [64 (v % nrt), +64) of the columns of pair
 // v / nrt, X <- X G, plus E = G - I on the pair's own rows when the basis is
 // carried as D = X - I.  Units are taken one at a time from the queue
 // counter *xq (zero at the start of the step), one unit ahead so that its
 // copies run under the current unit's product; CTAs that finish their inner
 // solve early take more.
-__device__ void run_basis_queue(int* xq, long long nX, long long nrt, int round, int nblk, long long npad,
+__device__ void run_basis_queue_simt(int* xq, long long nX, long long nrt, int round, int nblk, long long npad,
                                 float* __restrict__ X, const float* __restrict__ Gg, const float* __restrict__ Edg,
                                 int delta, float* sm, long long* s_next) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -516,6 +524,245 @@ __device__ void run_basis_queue(int* xq, long long nX, long long nrt, int round,
     }
 }
 
+// ---------------------------------------------------------------------------
+// basis units on the tensor cores: X <- X G for 128 rows of the pair's 64
+// columns, one tcgen05.mma chain of kind::tf32 (M = 128, N = 64, K = 8 per
+// instruction) into a TMEM accumulator.  FP32 accuracy from TF32 operands by
+// the three-term split x = hi + lo (hi: x with its low 13 mantissa bits
+// cleared, lo = x - hi exactly): X G ~ Xhi Ghi + Xhi Glo + Xlo Ghi, whose
+// dropped term and the truncation of lo are below 2^-20 of |X||G| per
+// product.  Operands are staged through registers into the K-major
+// 128-byte-swizzled shared-memory layout the matrix descriptors describe.
+// ---------------------------------------------------------------------------
+constexpr int TC_A_BYTES = 128 * 128;   // 128 rows x 32 K (FP32) = one swizzle column
+constexpr int TC_B_BYTES = 64 * 128;    // 64 rows x 32 K
+// layout inside the (1024-byte aligned) unit buffer: A hi [2 K-halves], A lo, B hi, B lo
+constexpr int TC_OFF_AHI = 0, TC_OFF_ALO = 2 * TC_A_BYTES, TC_OFF_BHI = 4 * TC_A_BYTES,
+              TC_OFF_BLO = 4 * TC_A_BYTES + 2 * TC_B_BYTES;
+constexpr int TC_BYTES = 4 * TC_A_BYTES + 4 * TC_B_BYTES;   // 96 KB
+constexpr int TC_TMEM_COLS = 64;
+static_assert(TC_BYTES + 1023 <= (int)BJ_SMEM, "tensor-core operands in the dynamic shared memory");
+// instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// byte offset of element (row r, k) (k < 32) in a K-major tile of 128-byte
+// rows with the 128-byte swizzle (16-byte chunk c of row r at c ^ (r mod 8))
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) << 4) | ((k & 3) << 2)));
+}
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading-dimension offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride between 8-row groups
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;   // exact: x and hi share sign and exponent
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit_to(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// bounded wait on the MMA completion barrier; false (and *err set) when the
+// bound runs out
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < (1LL << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+// Basis units of round `round` (G of that round in Gg row-major and Gcg
+// column-major, E's diagonal in Edg): unit v is the 128 rows
+// [128 (v % nrb), +128) of the columns of pair v / nrb, X <- X G, plus
+// E = G - I on the pair's own rows when the basis is carried as D = X - I.
+// Units are taken one at a time from the queue counter *xq (zero at the
+// start of the step); CTAs that finish their inner solve early take more.
+// tc: the CTA's TMEM accumulator, bar/phase: its MMA completion barrier.
+__device__ __forceinline__ void tc_tile_coords(int e, int& r4, int& c) {
+    const int ln = e & 31, grp = e >> 5;
+    r4 = (grp & 15) * 8 + (ln & 1) * 4;
+    c = (grp >> 4) * 16 + (ln >> 1);
+}
+
+// four of the thread's eight 16-byte loads of a 128 x 64 basis tile (half h)
+__device__ __forceinline__ void tc_load_half(const float* __restrict__ X, long long npad, int r0, int bi, int bj,
+                                             int h, float4 (&xv)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int r4, c;
+        tc_tile_coords(threadIdx.x + 256 * (4 * h + u), r4, c);
+        xv[u] = __ldcg(reinterpret_cast<const float4*>(X + r0 + r4 + (long long)sup_idx(c, bi, bj) * npad));
+    }
+}
+
+// split and swizzled stores of the loads of tc_load_half
+__device__ __forceinline__ void tc_store_half(unsigned char* tcs, int h, const float4 (&xv)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int r4, c;
+        tc_tile_coords(threadIdx.x + 256 * (4 * h + u), r4, c);
+        const float xs[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float hi, lo;
+            split_tf32(xs[i], hi, lo);
+            const uint32_t off = (uint32_t)((c >> 5) * TC_A_BYTES) + sw128_off(r4 + i, c & 31);
+            *reinterpret_cast<float*>(tcs + TC_OFF_AHI + off) = hi;
+            *reinterpret_cast<float*>(tcs + TC_OFF_ALO + off) = lo;
+        }
+    }
+}
+
+__device__ void run_basis_queue(int* xq, long long nX, long long nrb, int round, int nblk, long long npad,
+                                float* __restrict__ X, const float* __restrict__ Gg,
+                                const float* __restrict__ Gcg, const float* __restrict__ Edg, int delta,
+                                unsigned char* tcs, uint32_t tmem, uint64_t* bar, uint32_t& phase, int* err,
+                                long long* s_next) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // a software pipeline over the CTA's units: the queue index of the next
+    // unit is fetched, and the first half of its tile loaded, while the
+    // current unit's products run
+    if (tid == 0) *s_next = atomicAdd(xq, 1);
+    __syncthreads();
+    long long v = *s_next;
+    __syncthreads();
+    float4 xa[4];
+    if (v < nX) {
+        int bi, bj;
+        circle_pair(round, (int)(v / nrb), nblk, bi, bj);
+        tc_load_half(X, npad, (int)(v % nrb) * 128, bi, bj, 0, xa);
+    }
+    while (v < nX) {
+        if (tid == 0) *s_next = atomicAdd(xq, 1);
+        const int k = (int)(v / nrb), r0 = (int)(v % nrb) * 128;
+        int bi, bj;
+        circle_pair(round, k, nblk, bi, bj);
+        // A = X[r0 .. r0+128, pair k's columns]: a warp covers 8 rows (two
+        // lanes per column) x 16 columns, so each swizzled store hits 32
+        // distinct banks
+        tc_store_half(tcs, 0, xa);
+        tc_load_half(X, npad, r0, bi, bj, 1, xa);
+        // B = G as N x K (row n = column j of G, K = t)
+        const float* gc = Gcg + (long long)k * 4096;
+        tc_store_half(tcs, 1, xa);
+        for (int h8 = 0; h8 < 16; h8 += 8) {
+            float gv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int grp = (tid + 256 * (h8 + u)) >> 5;
+                const int nrow = (grp & 7) * 8 + (lane & 7), t = (grp >> 3) * 4 + (lane >> 3);
+                gv[u] = __ldcg(gc + nrow * 64 + t);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int grp = (tid + 256 * (h8 + u)) >> 5;
+                const int nrow = (grp & 7) * 8 + (lane & 7), t = (grp >> 3) * 4 + (lane >> 3);
+                float h, l;
+                split_tf32(gv[u], h, l);
+                const uint32_t off = (uint32_t)((t >> 5) * TC_B_BYTES) + sw128_off(nrow, t & 31);
+                *reinterpret_cast<float*>(tcs + TC_OFF_BHI + off) = h;
+                *reinterpret_cast<float*>(tcs + TC_OFF_BLO + off) = l;
+            }
+        }
+        // the operands, written by the generic proxy, are read by the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const long long vn = *s_next;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(tcs);
+            uint32_t acc = 0;
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ahi = sw128_desc(base + TC_OFF_AHI + kh * TC_A_BYTES) + 2 * kk;
+                    const uint64_t alo = sw128_desc(base + TC_OFF_ALO + kh * TC_A_BYTES) + 2 * kk;
+                    const uint64_t bhi = sw128_desc(base + TC_OFF_BHI + kh * TC_B_BYTES) + 2 * kk;
+                    const uint64_t blo = sw128_desc(base + TC_OFF_BLO + kh * TC_B_BYTES) + 2 * kk;
+                    tc_mma_tf32(tmem, alo, bhi, acc);
+                    acc = 1;
+                    tc_mma_tf32(tmem, ahi, blo, 1);
+                    tc_mma_tf32(tmem, ahi, bhi, 1);
+                }
+            tc_commit_to(bar);
+        }
+        // the next unit's first loads run under the products
+        if (vn < nX) {
+            int ni, nj;
+            circle_pair(round, (int)(vn / nrb), nblk, ni, nj);
+            tc_load_half(X, npad, (int)(vn % nrb) * 128, ni, nj, 0, xa);
+        }
+        // every thread waits; the outcome is made uniform (tcgen05.ld is a
+        // whole-warp instruction)
+        const bool done = __syncthreads_and(tc_wait(bar, phase, err) ? 1 : 0) != 0;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (done) {
+            // warp w reads TMEM lanes 32 (w mod 4) .. (rows) and columns 32 (w / 4) ..
+            const int q = warp & 3, ch = warp >> 2;
+            const int r = q * 32 + lane, g = r0 + r;
+            int t0 = -1;
+            if (delta) {
+                const int blk = g >> 5;
+                if (blk == bi) t0 = g - bi * 32;
+                else if (blk == bj) t0 = 32 + g - bj * 32;
+            }
+            for (int half = 0; half < 2; ++half) {
+                uint32_t vv[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32 + half * 16), vv);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = ch * 32 + half * 16 + c;
+                    float z = __uint_as_float(vv[c]);
+                    if (t0 >= 0)
+                        z += (t0 == j) ? __ldcg(Edg + (long long)k * 64 + t0)
+                                       : __ldcg(Gg + (long long)k * 4096 + t0 * 64 + j);
+                    X[g + (long long)sup_idx(j, bi, bj) * npad] = z;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // shared operands and the accumulator free again; s_next read by all
+        v = vn;
+    }
+}
+
 // The whole iteration in one cooperative launch.  Per round r:
 //   step 1  inner solves of round r (one CTA per pair) and the basis update
 //           of round r - 1 (it only needs E of that round, kept in the other
@@ -528,6 +775,7 @@ __device__ void run_basis_queue(int* xq, long long nX, long long nrt, int round,
 //   delta = 0: S = fl32(A) (its diagonal too), basis X = I;  out = X
 //   delta = 1: S = B with the FP64 diagonal, D = 0;           out = D
 // acc[4] must be zero at launch (the scale's maximum is reduced into it).
+template <bool TC>
 __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __restrict__ A, long long lda, int n,
                                                                float* ws, float* __restrict__ out, int max_sweeps,
                                                                int inner_sweeps, int delta, double stop_tol,
@@ -537,9 +785,33 @@ __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __r
     __shared__ unsigned short ptab[63 * 32];
     __shared__ double s_off[BJ_NT / 32], s_all[BJ_NT / 32];
     __shared__ long long s_chunk;
+    __shared__ __align__(8) uint64_t tc_bar;   // completion of the basis unit's MMA chain
+    __shared__ uint32_t tc_slot;                // TMEM address of the accumulator
     const long long npad = bj_npad(n), nn = npad * npad;
     const BjWs w = bj_ws(ws, n);
     int* xq = w.slots + 2;   // basis-unit queue of the current step 1
+    int* tc_err = w.slots + 3;   // set when a wait for the tensor cores runs out
+    // the tensor cores' operand buffer: 1024-byte aligned for the swizzle
+    unsigned char* tcs = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(sm) + 1023) & ~(uintptr_t)1023);
+    if (TC) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tc_bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&tc_slot)),
+                         "r"(TC_TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (TC) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = TC ? tc_slot : 0u;
+    uint32_t tc_phase = 0;
     const int nblk = (int)(npad / 32), npairs = nblk / 2;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -585,11 +857,15 @@ __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __r
         w.dg[p] = d;
     }
     if (gtid < 4) w.acc[gtid] = 0.0;
-    if (gtid == 0) *xq = 0;
+    if (gtid == 0) {
+        *xq = 0;
+        *tc_err = 0;
+    }
     grid.sync();
     const long long nA = (long long)npairs * (npairs - 1) / 2;
-    const long long nrt = npad / 64;
-    const long long nX = nrt * npairs;
+    const long long nrb = npad / 128, nrt = npad / 64;
+    const long long nX = nrb * npairs;    // tensor-core basis units (128 rows)
+    const long long nXs = nrt * npairs;   // FP32-pipe basis units (64 rows)
     long long ax_lo, ax_hi;
     unit_range(nA, blockIdx.x, gridDim.x, ax_lo, ax_hi);
     const long long gbuf = (long long)npairs * 4096, ebuf = (long long)npairs * 64;
@@ -600,12 +876,19 @@ __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __r
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < nblk - 1; ++r, ++gr) {
             float* Gr = w.G + (gr & 1) * gbuf;
+            float* Gcr = w.Gc + (gr & 1) * gbuf;
             float* Er = w.Ed + (gr & 1) * ebuf;
             for (int k = blockIdx.x; k < npairs; k += gridDim.x)
-                bj_inner(k, r, nblk, npad, w.O, w.dg, Gr, Er, inner_sweeps, sm, ptab);
-            if (pend_round >= 0)
-                run_basis_queue(xq, nX, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
-                                w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
+                bj_inner(k, r, nblk, npad, w.O, w.dg, Gr, Gcr, Er, inner_sweeps, sm, ptab);
+            if (pend_round >= 0) {
+                if (!TC || delta)
+                    run_basis_queue_simt(xq, nXs, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                                         w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
+                else
+                    run_basis_queue(xq, nX, nrb, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                                    w.Gc + ((gr - 1) & 1) * gbuf, w.Ed + ((gr - 1) & 1) * ebuf, delta, tcs, tmem,
+                                    &tc_bar, tc_phase, tc_err, &s_chunk);
+            }
             grid.sync();
             if (gtid == 0) *xq = 0;   // nobody takes from the queue until the next step 1
             run_off_units(ax_lo, ax_hi, npairs, r, nblk, npad, w.O, Gr, sm);
@@ -660,9 +943,15 @@ __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __r
         grid.sync();   // the other slot is zero before anyone adds to it
     }
     // the last round's basis update
-    if (pend_round >= 0)
-        run_basis_queue(xq, nX, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
-                        w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
+    if (pend_round >= 0) {
+        if (!TC || delta)
+            run_basis_queue_simt(xq, nXs, nrt, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                                 w.Ed + ((gr - 1) & 1) * ebuf, delta, sm, &s_chunk);
+        else
+            run_basis_queue(xq, nX, nrb, pend_round, nblk, npad, w.X, w.G + ((gr - 1) & 1) * gbuf,
+                            w.Gc + ((gr - 1) & 1) * gbuf, w.Ed + ((gr - 1) & 1) * ebuf, delta, tcs, tmem, &tc_bar,
+                            tc_phase, tc_err, &s_chunk);
+    }
     grid.sync();
     if (blockIdx.x == 0 && threadIdx.x == 0) w.slots[slot] = done;
     // indices never move, so the basis is in the original column order;
@@ -672,19 +961,33 @@ __global__ void __launch_bounds__(BJ_NT, 2) bjac32_coop_kernel(const double* __r
         const int r = (int)(e % n), c = (int)(e / n);
         out[e] = __ldcg(w.X + r + (long long)c * npad);
     }
+    if (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                         : "memory");
+        }
+    }
 }
 
 int bj_inner_sweeps() { return 1; }
 
 cudaError_t bj_launch(const double* A, long long lda, int n, float* out, float* ws, int max_sweeps, int delta,
                       double stop_tol, int slot, int max_grid, cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(bjac32_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BJ_SMEM);
+    // the tensor cores take the first pass's basis updates while the two
+    // FP32 matrices fit in L2 (npad <= 2048: 32 MB); at larger orders the
+    // units' staging through registers waits on DRAM and the FP32-pipe
+    // units with their asynchronous copies are faster (measured at 4096)
+    const bool tc = delta == 0 && bj_npad(n) <= 2048;
+    const void* kern = tc ? (const void*)bjac32_coop_kernel<true> : (const void*)bjac32_coop_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BJ_SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bjac32_coop_kernel, BJ_NT, BJ_SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BJ_NT, BJ_SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const BjWs w = bj_ws(ws, n);
@@ -692,13 +995,13 @@ cudaError_t bj_launch(const double* A, long long lda, int n, float* out, float* 
     if (e != cudaSuccess) return e;
     const long long npad = bj_npad(n);
     const long long npairs = npad / 64;
-    const long long units = std::max(npairs * (npairs - 1) / 2, npairs + (npad / 64) * npairs);
+    const long long units = std::max(npairs * (npairs - 1) / 2, npairs + (npad / 128) * npairs);
     int grid = (int)std::min<long long>((long long)sms * std::min(per_sm, 2), units);
     if (max_grid > 0 && grid > max_grid) grid = max_grid;   // share the GPU (all CTAs must be co-resident)
     int inner = bj_inner_sweeps();
     void* args[] = {(void*)&A,      (void*)&lda,   (void*)&n,        (void*)&ws,   (void*)&out,
                     (void*)&max_sweeps, (void*)&inner, (void*)&delta, (void*)&stop_tol, (void*)&slot};
-    return cudaLaunchCooperativeKernel((const void*)bjac32_coop_kernel, dim3(grid), dim3(BJ_NT), args, BJ_SMEM,
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(BJ_NT), args, BJ_SMEM,
                                        st);
 }
 
@@ -706,7 +1009,7 @@ cudaError_t bj_launch(const double* A, long long lda, int n, float* out, float* 
 
 size_t diag_fp32_ws_floats(int n) {
     const long long npad = bj_npad(n), npairs = npad / 64;
-    return (size_t)(2 * npad * npad + 2 * npad + 2 * npairs * (4096 + 64) + 16 + 16);   // ... acc[8] | slots[3]
+    return (size_t)(2 * npad * npad + 2 * npad + 2 * npairs * (2 * 4096 + 64) + 16 + 16);   // ... acc[8] | slots[3]
 }
 
 // Q0 <- eigenvectors of fl32(A) (n x n, ld n).  ws: diag_fp32_ws_floats(n)
@@ -728,7 +1031,9 @@ cudaError_t refine_fp32(const double* B, int n, float* Dout, float* ws, int max_
 // attributes loads it, where a first launch would otherwise do so later.
 cudaError_t preload_diag32_kernels() {
     cudaFuncAttributes fa;
-    return cudaFuncGetAttributes(&fa, bjac32_coop_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, bjac32_coop_kernel<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, bjac32_coop_kernel<false>);
+    return e;
 }
 
 // Sweeps made by the last diag_fp32 / refine_fp32 launches on workspace ws
