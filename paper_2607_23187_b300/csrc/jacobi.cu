@@ -72,6 +72,8 @@ struct Sh {
     Slot inbox[2][16];      // slot of every cluster rank, pushed by the sender
     Slot stage;             // this CTA's slot before it is pushed
     Cand sel;
+    Cand sel3[3];           // cta_select3: the warps' final selections (1 and 2 used)
+    int kk3[4];             // cta_select3: the merged keys of rows i and j
     int tflag, pad3;
     double c, s, t, dii, djj, q;
     double cs[48][2];       // (c, s) of every published candidate (3 per cluster rank)
@@ -381,27 +383,32 @@ __device__ void cta_select3(Cand& c0, Cand& c1, Cand& c2, int pivot, const doubl
         sh.wkk[warp][0] = kA[0]; sh.wkk[warp][1] = kA[1]; sh.wkk[warp][2] = kB[0]; sh.wkk[warp][3] = kB[1];
     }
     __syncthreads();
-    if (warp != 0) return;
-    Cand r[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        Cand c = (lane < NT / 32) ? sh.ww[lane][q] : no_cand();
+    if (warp >= 4) return;
+    // warps 0-2 select one of the three candidates each, warp 3 merges the
+    // keys; warp 0 collects after a barrier of these four warps
+    if (warp < 3) {
+        Cand c = (lane < NT / 32) ? sh.ww[lane][warp] : no_cand();
         Cand* wb = nullptr;
-        if (q == 0 && c.key != KEY_NONE && c.row >= k0 && c.row < k1) wb = &cache[c.row - k0];
-        r[q] = warp_select(c, pivot, diag, wb);
-    }
-    c0 = r[0];
-    c1 = r[1];
-    c2 = r[2];
-    int a1 = KEY_NONE, a2 = KEY_NONE, b1 = KEY_NONE, b2 = KEY_NONE;
+        if (warp == 0 && c.key != KEY_NONE && c.row >= k0 && c.row < k1) wb = &cache[c.row - k0];
+        const Cand r = warp_select(c, pivot, diag, wb);
+        if (warp == 0) c0 = r;
+        else if (lane == 0) sh.sel3[warp] = r;
+    } else if (lane == 0) {
+        int a1 = KEY_NONE, a2 = KEY_NONE, b1 = KEY_NONE, b2 = KEY_NONE;
 #pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        key_push(sh.wkk[w][0], a1, a2);
-        key_push(sh.wkk[w][1], a1, a2);
-        key_push(sh.wkk[w][2], b1, b2);
-        key_push(sh.wkk[w][3], b1, b2);
+        for (int w = 0; w < NT / 32; ++w) {
+            key_push(sh.wkk[w][0], a1, a2);
+            key_push(sh.wkk[w][1], a1, a2);
+            key_push(sh.wkk[w][2], b1, b2);
+            key_push(sh.wkk[w][3], b1, b2);
+        }
+        sh.kk3[0] = a1; sh.kk3[1] = a2; sh.kk3[2] = b1; sh.kk3[3] = b2;
     }
-    kA[0] = a1; kA[1] = a2; kB[0] = b1; kB[1] = b2;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (warp != 0) return;
+    c1 = sh.sel3[1];
+    c2 = sh.sel3[2];
+    kA[0] = sh.kk3[0]; kA[1] = sh.kk3[1]; kB[0] = sh.kk3[2]; kB[1] = sh.kk3[3];
 }
 
 __device__ __forceinline__ double block_sum(double v, Sh& sh) {
