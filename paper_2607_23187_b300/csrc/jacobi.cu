@@ -73,6 +73,9 @@ struct Sh {
     Slot stage;             // this CTA's slot before it is pushed
     Cand sel;
     Cand sel3[3];           // cta_select3: the warps' final selections (1 and 2 used)
+    int rk[32], rc[32];     // rescan_row_keys: each warp's four largest keys and their columns
+    Cand rs_b, rs_s;        // rescan_row_keys: the row's head and second entry
+    int rs_f, rs_ok;        // rescan_row_keys: the key bound; 0 when the full rescan is needed
     int kk3[4];             // cta_select3: the merged keys of rows i and j
     int tflag, pad3;
     double c, s, t, dii, djj, q;
@@ -87,6 +90,8 @@ struct Sh {
 #endif
 };
 
+// the key-based rescan merges four entries of each warp in one warp
+static_assert((NT / 32) * 4 == 32, "rescan_row_keys expects eight warps");
 // warps 5 and up finish (c, s) of the 3 candidates of each of up to 16 ranks
 static_assert((NT / 32 - 5) * 32 >= 48, "too few warps for the cosines of the published candidates");
 
@@ -528,13 +533,15 @@ __device__ Cand rescan_row(const JacArgs& a, int k, const double* diag, Sh& sh, 
 
 // off(A)^2 * 2^-2e over the owned rows, e = ilogb(||A1||_F) (as the oracle).
 // Row rescan from the stored keys (column k of K holds the keys of row k):
-// each thread keeps the four largest keys of its columns; the head b is the
-// exact maximum among the entries within the tie band of the largest key,
-// sec the exact best of the listed entries other than b, and F the largest
-// listed key other than b's and sec's (an entry left out of a thread's list
-// has a key no larger than that thread's smallest listed key).  Returns
-// false, with nothing written, when some thread's list is full of
-// contenders for the maximum: then only the full rescan is exact.
+// each thread keeps the four largest keys of its columns, each warp the four
+// largest of its threads' lists, and warp 0 merges the warps' lists: the
+// head b is the exact maximum among the entries within the tie band of the
+// largest key, sec the exact best of the listed entries other than b, and F
+// the largest listed key other than b's and sec's (an entry left out of a
+// list has a key no larger than that list's smallest).  One block barrier
+// besides the final one.  Returns false, with nothing written, when some
+// warp's list is full of contenders for the maximum: then only the full
+// rescan is exact.
 __device__ bool rescan_row_keys(const JacArgs& a, int k, const double* diag, Sh& sh, Cand& b, Cand& sec,
                                 int& F) {
     const int* kr = a.K + (long long)k * a.ldk;
@@ -561,39 +568,69 @@ __device__ bool rescan_row_keys(const JacArgs& a, int k, const double* diag, Sh&
                 }
         }
     }
-    const int kmax = block_max_int(lk[0], sh);
-    if (kmax == KEY_NONE) {
-        b = no_cand(); sec = no_cand(); F = KEY_NONE;
-        return true;
-    }
-    const bool gap = a.pivot != PJAC_PIVOT_GREEDY;
-    const bool exact_all = gap && kmax < KEY_SUB;
-    const int tie = gap ? KEY_GAP_TIE : 0;
-    const bool ovf = lk[3] != KEY_NONE && (exact_all || (long long)lk[3] >= (long long)kmax - tie);
-    if (__syncthreads_or(ovf)) return false;
-    Cand e[4];
+    // each warp's four largest keys: four rounds of the maximum over the
+    // lanes' list heads, popped at the first lane that holds it
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int wk = KEY_NONE, wc = -1;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        e[q] = no_cand();
-        if (lk[q] != KEY_NONE) {
-            e[q].key = lk[q]; e[q].row = k; e[q].col = lc[q]; e[q].x = ldcg(row + lc[q]);
+        const int m = __reduce_max_sync(0xffffffffu, lk[0]);
+        const int src = __ffs(__ballot_sync(0xffffffffu, lk[0] == m)) - 1;
+        const int col = __shfl_sync(0xffffffffu, lc[0], src);
+        if (lane == q) { wk = m; wc = col; }
+        if (lane == src) {
+            lk[0] = lk[1]; lc[0] = lc[1];
+            lk[1] = lk[2]; lc[1] = lc[2];
+            lk[2] = lk[3]; lc[2] = lc[3];
+            lk[3] = KEY_NONE; lc[3] = -1;
         }
     }
-    Cand m = no_cand();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (better(e[q], m, a.pivot, diag)) m = e[q];
-    b = block_select(m, a.pivot, diag, sh);
-    Cand m2 = no_cand();
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (e[q].col != b.col && better(e[q], m2, a.pivot, diag)) m2 = e[q];
-    sec = block_select(m2, a.pivot, diag, sh);
-    int r = KEY_NONE;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (lc[q] >= 0 && lc[q] != b.col && lc[q] != sec.col) r = max(r, lk[q]);
-    F = block_max_int(r, sh);
+    if (lane < 4) {
+        sh.rk[warp * 4 + lane] = wk;
+        sh.rc[warp * 4 + lane] = wc;
+    }
+    __syncthreads();
+    // warp 0 merges the 32 listed entries (lane l: entry l mod 4 of warp l / 4)
+    if (warp == 0) {
+        const int ek = sh.rk[lane], ec = sh.rc[lane];
+        const int kmax = __reduce_max_sync(0xffffffffu, ek);
+        int ok = 1;
+        Cand bb = no_cand(), ss = no_cand();
+        int ff = KEY_NONE;
+        if (kmax != KEY_NONE) {
+            const bool gap = a.pivot != PJAC_PIVOT_GREEDY;
+            const bool exact_all = gap && kmax < KEY_SUB;
+            const int tie = gap ? KEY_GAP_TIE : 0;
+            // a warp whose fourth entry contends for the maximum may have left
+            // contenders out: then only the full rescan is exact
+            const bool ovf = (lane & 3) == 3 && ek != KEY_NONE &&
+                             (exact_all || (long long)ek >= (long long)kmax - tie);
+            if (__any_sync(0xffffffffu, ovf)) {
+                ok = 0;
+            } else {
+                Cand c = no_cand();
+                if (ek != KEY_NONE) {
+                    c.key = ek; c.row = k; c.col = ec; c.x = ldcg(row + ec);
+                }
+                bb = warp_select(c, a.pivot, diag, nullptr);
+                const Cand c2 = (c.key != KEY_NONE && c.col != bb.col) ? c : no_cand();
+                ss = warp_select(c2, a.pivot, diag, nullptr);
+                const int rk = (ek != KEY_NONE && ec != bb.col && ec != ss.col) ? ek : KEY_NONE;
+                ff = __reduce_max_sync(0xffffffffu, rk);
+            }
+        }
+        if (lane == 0) {
+            sh.rs_ok = ok;
+            sh.rs_b = bb;
+            sh.rs_s = ss;
+            sh.rs_f = ff;
+        }
+    }
+    __syncthreads();
+    if (!sh.rs_ok) return false;
+    b = sh.rs_b;
+    sec = sh.rs_s;
+    F = sh.rs_f;
     return true;
 }
 
