@@ -53,7 +53,7 @@ struct Cand {
 };
 
 struct Slot {
-    Cand loc, pi, pj;       // this CTA's best own row, its part of row i, of row j
+    Cand cand[3];           // this CTA's best own row, its part of row i, of row j
     int ki[2], kj[2];       // the two largest keys of its parts of rows i and j
     double prm[3][3];       // (den, 4q^2, t) of each candidate's rotation (scaled; rot_cs gives c, s)
     double sum;
@@ -109,6 +109,12 @@ __device__ __forceinline__ unsigned int& prof_exact() {
 #define PROF_ADD(k, v) ((void)0)
 #endif
 
+// Scores are non-negative doubles (or a negative "not evaluated" sentinel);
+// such values order like their bit patterns read as signed integers, so
+// they are compared on the integer pipes (an FP64 compare waits on the
+// FP64 pipe's long latency).
+__device__ __forceinline__ long long sbits(double v) { return __double_as_longlong(v); }
+
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg(double* p, double v) { __stcg(p, v); }
 
@@ -125,7 +131,7 @@ __device__ __forceinline__ int entry_key(int pivot, double x, double dd) {
 // Exact score of a candidate (gap: Eq. (1.1) in FP64; greedy: |x|).
 __device__ __forceinline__ double cand_value(Cand& c, int pivot, const double* diag) {
     if (pivot == PJAC_PIVOT_GREEDY) return fabs(c.x);
-    if (c.ex < 0.0) {
+    if (sbits(c.ex) < 0) {   // not evaluated yet
         c.ex = gap_exact(diag[c.row], diag[c.col], c.x);
 #ifdef PJAC_PROFILE
         if (c.x != 0.0) atomicAdd(&prof_exact(), 1u);
@@ -135,7 +141,7 @@ __device__ __forceinline__ double cand_value(Cand& c, int pivot, const double* d
 }
 
 __device__ __forceinline__ bool exact_better(double va, const Cand& a, double vb, const Cand& b) {
-    if (va != vb) return va > vb;
+    if (sbits(va) != sbits(vb)) return sbits(va) > sbits(vb);
     if (a.row != b.row) return a.row < b.row;
     return a.col < b.col;
 }
@@ -283,12 +289,13 @@ __device__ Cand block_select(Cand mine, int pivot, const double* diag, Sh& sh) {
         int orr = __shfl_xor_sync(0xffffffffu, br, off);
         int oc = __shfl_xor_sync(0xffffffffu, bc, off);
         int ol = __shfl_xor_sync(0xffffffffu, bl, off);
-        bool take = (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
+        const long long ob = sbits(ov), bb = sbits(bv);
+        bool take = (ob > bb) || (ob == bb && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
         if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
     }
     if (lane == bl) {
         Cand w = mine;
-        if (bv < -1.0) w.key = KEY_NONE;
+        if (sbits(bv) < 0) w.key = KEY_NONE;   // no contender (the -2 sentinel)
         sh.wc[threadIdx.x >> 5] = w;
     }
     __syncthreads();
@@ -350,8 +357,9 @@ __device__ Cand warp_select(Cand c, int pivot, const double* diag, Cand* wb) {
                 const int orr = __shfl_xor_sync(0xffffffffu, br, off);
                 const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
                 const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+                const long long ob = sbits(ov), bb = sbits(bv);
                 const bool take =
-                    (ov > bv) || (ov == bv && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
+                    (ob > bb) || (ob == bb && (orr < br || (orr == br && (oc < bc || (oc == bc && ol < bl)))));
                 if (take) { bv = ov; br = orr; bc = oc; bl = ol; }
             }
             src = bl;
@@ -1006,9 +1014,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     rq = ev.q4;
                     rt = ev.t;
                 }
-                if (tid == 0) sh.stage.loc = c;
-                else if (tid == 1) sh.stage.pi = c;
-                else sh.stage.pj = c;
+                sh.stage.cand[tid] = c;
                 sh.stage.prm[tid][0] = rd;
                 sh.stage.prm[tid][1] = rq;
                 sh.stage.prm[tid][2] = rt;
@@ -1065,7 +1071,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 for (int e = lane; e < 3 * P; e += 32) {
                     const Slot& sl = sh.inbox[par][e / 3];
                     const int q3 = e - 3 * (e / 3);
-                    Cand c = (q3 == 0) ? sl.loc : (q3 == 1 ? sl.pi : sl.pj);
+                    Cand c = sl.cand[q3];
                     c.pad = e;
                     if (better(c, g, pivot, diag)) g = c;
                 }
@@ -1078,17 +1084,17 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                     if (g.key == KEY_NONE) dec = 1;   // n < 2
                     else if (pivot == PJAC_PIVOT_GREEDY) {
                         v = fabs(g.x);
-                        if (v == 0.0) dec = 1;
+                        if (sbits(v) == 0) dec = 1;
                     } else {
                         v = cand_value(g, pivot, diag);   // exact score published with the candidate
-                        if (v == 0.0) dec = 1;
-                        if (!dec && a.stop == PJAC_STOP_LIBOUND && v <= sh.eps_li) dec = 1;
+                        if (sbits(v) == 0) dec = 1;
+                        if (!dec && a.stop == PJAC_STOP_LIBOUND && sbits(v) <= sbits(sh.eps_li)) dec = 1;
                     }
                     if (!dec && rot >= a.max_rot) dec = 3;
                     if (sh.inbox[par][0].flags & 1) dec = 2;   // time budget spent
                     sh.decision = dec;
                     sh.sel = g;
-                    if (v >= 0.0) sh.q = v;
+                    if (sbits(v) >= 0) sh.q = v;
                     if (!dec) {
                         const int i2 = min(g.row, g.col), j2 = max(g.row, g.col);
                         const double* pr = sh.inbox[par][g.pad / 3].prm[g.pad % 3];
@@ -1113,7 +1119,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
                 int ka = KEY_NONE, kb = KEY_NONE;   // two largest keys of the row
                 if (lane < P) {
                     const Slot& sl = sh.inbox[par][lane];
-                    c = (warp == 1) ? sl.pi : sl.pj;
+                    c = sl.cand[warp];
                     c.pad = lane * 3 + warp;
                     ka = (warp == 1) ? sl.ki[0] : sl.kj[0];
                     kb = (warp == 1) ? sl.ki[1] : sl.kj[1];
