@@ -31,15 +31,29 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
+// The scaling exponent: ilogb(m) when m = max(|d|, |q|) > 2^500 or
+// m < 2^-500, else 0.  Non-negative doubles order as their bit patterns, so
+// the maximum and both tests are integer operations (an FP64 compare waits
+// on the FP64 pipe's long latency).
 __device__ __forceinline__ int scale_exp(double d, double q) {
-    double m = fmax(fabs(d), fabs(q));
-    if (m > 0x1p+500 || m < 0x1p-500) return ilogb(m);
+    const unsigned long long ud = (unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffULL;
+    const unsigned long long uq = (unsigned long long)__double_as_longlong(q) & 0x7fffffffffffffffULL;
+    const unsigned long long um = ud > uq ? ud : uq;
+    if (um > 0x5F30000000000000ULL || um < 0x20B0000000000000ULL)   // 2^500, 2^-500
+        return ilogb(__longlong_as_double((long long)um));
     return 0;
+}
+
+// t negated when d != 0 and sign(d) != sign(q), tested on the sign bits
+__device__ __forceinline__ bool opposite_nonzero(double d, double q) {
+    const unsigned long long bd = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long bq = (unsigned long long)__double_as_longlong(q);
+    return (bd & 0x7fffffffffffffffULL) != 0 && ((bd ^ bq) >> 63) != 0;
 }
 
 // Eq. (1.1) for diagonal entries dii, djj and off-diagonal q.
 __device__ __forceinline__ double gap_exact(double dii, double djj, double q) {
-    if (q == 0.0) return 0.0;
+    if ((__double_as_longlong(q) & 0x7fffffffffffffffLL) == 0) return 0.0;
     double d = __dadd_rn(dii, -djj);
     int e = scale_exp(d, q);
     if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
@@ -55,7 +69,7 @@ struct Rot { double c, s, t; };
 
 __device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
     Rot r;
-    if (q == 0.0) { r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
+    if ((__double_as_longlong(q) & 0x7fffffffffffffffLL) == 0) { r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
     double d = __dadd_rn(dii, -djj);
     int e = scale_exp(d, q);
     if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
@@ -64,7 +78,7 @@ __device__ __forceinline__ Rot rot_params(double dii, double djj, double q) {
     double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(d, d), q4));
     double den = __dadd_rn(fabs(d), rr);
     double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
-    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    if (opposite_nonzero(d, q)) t = -t;
     double c = __ddiv_rn(den, __dsqrt_rn(__dadd_rn(__dmul_rn(den, den), q4)));
     r.t = t;
     r.c = c;
@@ -79,7 +93,7 @@ struct Eval { double l, c, s, t; };
 
 __device__ __forceinline__ Eval eval_pair(double dii, double djj, double q) {
     Eval r;
-    if (q == 0.0) { r.l = 0.0; r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
+    if ((__double_as_longlong(q) & 0x7fffffffffffffffLL) == 0) { r.l = 0.0; r.c = 1.0; r.s = 0.0; r.t = 0.0; return r; }
     double d = __dadd_rn(dii, -djj);
     int e = scale_exp(d, q);
     if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
@@ -90,7 +104,7 @@ __device__ __forceinline__ Eval eval_pair(double dii, double djj, double q) {
     double l = __ddiv_rn(__dmul_rn(2.0, q2), den);
     if (e != 0) l = ldexp(l, e);
     double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
-    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    if (opposite_nonzero(d, q)) t = -t;
     double c = __ddiv_rn(den, __dsqrt_rn(__dadd_rn(__dmul_rn(den, den), q4)));
     r.l = l;
     r.t = t;
@@ -107,7 +121,10 @@ struct EvalHead { double l, t, den, q4; };
 
 __device__ __forceinline__ EvalHead eval_pair_head(double dii, double djj, double q) {
     EvalHead r;
-    if (q == 0.0) { r.l = 0.0; r.t = 0.0; r.den = 1.0; r.q4 = 0.0; return r; }   // rot_cs: c = 1, s = 0
+    if ((__double_as_longlong(q) & 0x7fffffffffffffffLL) == 0) {   // q == 0 (rot_cs: c = 1, s = 0)
+        r.l = 0.0; r.t = 0.0; r.den = 1.0; r.q4 = 0.0;
+        return r;
+    }
     double d = __dadd_rn(dii, -djj);
     int e = scale_exp(d, q);
     if (e != 0) { d = ldexp(d, -e); q = ldexp(q, -e); }
@@ -118,7 +135,7 @@ __device__ __forceinline__ EvalHead eval_pair_head(double dii, double djj, doubl
     double l = __ddiv_rn(__dmul_rn(2.0, q2), den);
     if (e != 0) l = ldexp(l, e);
     double t = __ddiv_rn(__dmul_rn(2.0, fabs(q)), den);
-    if (d != 0.0 && ((d < 0.0) != (q < 0.0))) t = -t;
+    if (opposite_nonzero(d, q)) t = -t;
     r.l = l;
     r.t = t;
     r.den = den;
