@@ -1173,6 +1173,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             publish_select(loc, no_cand(), no_cand(), kn, kn, -1, -1, false, 1.0, 0.0);
         }
         bool stop_now = false;
+        long long until_check = 0;   // rotations to the next convergence test (rot mod ce == 0)
         for (;;) {
             LAP(7);
 #ifdef PJAC_PROFILE
@@ -1180,7 +1181,8 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
 #endif
             if (pdec == 2) { status = PJAC_ETIMEOUT; break; }
             if (pdec == 0) preload(ppi, ppj);   // the loads do not depend on the test below
-            if (rot % ce == 0) {
+            if (until_check == 0) {
+                until_check = ce;
                 offdiag_check(stop_now);
                 if (stop_now) {
                     if (tid == 0 && pdec == 0) {   // the pending rotation is not applied
@@ -1202,6 +1204,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
             rotate_owned(i, j, c, s, dii, djj, true, false, pI, pJ, kI, kJ);
             SLAP(4);
             rot++;
+            --until_check;
             __syncthreads();
             LAP(2);
             // rescans of owned rows whose best was in column i or j
