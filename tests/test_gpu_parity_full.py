@@ -180,7 +180,7 @@ def test_serving_vs_oracle_solve(pj):
 # --------------------------------------------------------------------------
 # the GPU's low-precision eigenbasis Q0
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("cfg,n", [("cfg1", None), ("cfg2", 300), ("cfg2", 1024), ("cfg3", 2048)])
+@pytest.mark.parametrize("cfg,n", [("cfg1", None), ("cfg2", 300), ("cfg2", 1024), ("cfg3", 2048), ("cfg3", 4096)])
 def test_gpu_q0_validity(pj, h, cfg, n):
     p = pin.config_problem(cfg, n=n)
     nn = p.a.shape[0]
@@ -195,8 +195,8 @@ def test_gpu_q0_validity(pj, h, cfg, n):
     assert off <= c2 * nn * U32 * np.linalg.norm(p.a), off / (nn * U32 * np.linalg.norm(p.a))
     # and the GPU's Q0 works as the oracle's preconditioner: the Jacobi
     # iteration on the resulting A1 converges to the known spectrum
-    q, a1 = oracle.precondition(p.a, q0.astype(np.float32))
     if nn <= 300:
+        q, a1 = oracle.precondition(p.a, q0.astype(np.float32))
         r = oracle.jacobi(a1, q, pivot="gap", tol=1e-15)
         w, _ = oracle.readout(r["a"], r["v"])
         assert np.max(np.abs(w - p.lam)) <= 1e-13 * p.norm2
