@@ -181,46 +181,48 @@ __device__ __forceinline__ float mant23(unsigned long long b) {
     return __int_as_float(0x3f800000u | (unsigned)((b >> 29) & 0x7fffffu));
 }
 
-__device__ __forceinline__ int gap_key(double x, double dd) {
-    unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
-    if (bx == 0) return KEY_ZERO;
-    unsigned long long bd = (unsigned long long)__double_as_longlong(dd) & 0x7fffffffffffffffULL;
-    int ex = (int)(bx >> 52), ed = (int)(bd >> 52);
-    int adj = 0;
-    if (ex == 0 || (ed == 0 && bd != 0)) {
-        // subnormal operand: scale both by 2^64 (exact), remember the shift
-        bx = (unsigned long long)__double_as_longlong(__dmul_rn(fabs(x), 0x1p64));
-        bd = (unsigned long long)__double_as_longlong(__dmul_rn(fabs(dd), 0x1p64));
-        ex = (int)(bx >> 52);
-        ed = (int)(bd >> 52);
-        adj = 64;
-    }
-    float mx = mant23(bx);
-    int exu = ex - 1023 - adj;
-    int ip;
-    float f;
-    if (bd == 0) {
-        ip = exu;
-        f = __log2f(mx);
+// Unbiased exponent and the top 23 mantissa bits of a non-negative double
+// (magnitude bit pattern b != 0), subnormals normalised with integer shifts
+// (the leading one moved to the implicit bit).
+__device__ __forceinline__ void split_bits(unsigned long long b, int& e, float& m23) {
+    const int ef = (int)(b >> 52);
+    unsigned long long mb = b & 0x000fffffffffffffULL;
+    if (ef == 0) {
+        const int lz = __clzll((long long)mb);      // >= 12
+        mb = (mb << (lz - 11)) & 0x000fffffffffffffULL;
+        e = -1011 - lz;
     } else {
-        float md = mant23(bd);
-        int e = ed - ex;
-        if (e >= 60) {             // L ~ x^2/|d|
-            ip = 2 * exu - (ed - 1023 - adj);
-            f = __log2f(__fdividef(mx * mx, md));
-        } else if (e <= -60) {     // L ~ |x|
-            ip = exu;
-            f = __log2f(mx);
-        } else {
-            float rho = __fdividef(md, mx) * __int_as_float((e + 127) << 23);
-            float v = __fmaf_rn(rho, rho, 4.0f);
-            float g = __fdividef(2.0f, rho + v * rsqrtf(v));
-            ip = exu;
-            f = __log2f(mx * g);
-        }
+        e = ef - 1023;
     }
+    m23 = mant23(mb);
+}
+
+// Branch-free: every case's operands are formed and the argument of the one
+// logarithm is selected, so that two keys of one thread interleave.
+__device__ __forceinline__ int gap_key(double x, double dd) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    const unsigned long long bd = (unsigned long long)__double_as_longlong(dd) & 0x7fffffffffffffffULL;
+    int exu, edu;
+    float mx, md;
+    split_bits(bx | (bx == 0), exu, mx);            // (x == 0 is answered at the end)
+    split_bits(bd | (bd == 0), edu, md);
+    const int e = edu - exu;
+    // |d| far below |x| (or d == 0): L ~ |x|
+    float arg = mx;
+    int ip = exu;
+    if (bd != 0 && e >= 60) {                        // |d| far above |x|: L ~ x^2/|d|
+        arg = __fdividef(mx * mx, md);
+        ip = 2 * exu - edu;
+    } else if (bd != 0 && e > -60) {
+        const float rho = __fdividef(md, mx) * __int_as_float((e + 127) << 23);
+        const float v = __fmaf_rn(rho, rho, 4.0f);
+        const float g = __fdividef(2.0f, rho + v * rsqrtf(v));
+        arg = mx * g;
+    }
+    const float f = __log2f(arg);
     if (ip < -2040) ip = -2040;
-    return ip * (1 << 20) + __float2int_rd(f * 1048576.0f);
+    const int key = ip * (1 << 20) + __float2int_rd(f * 1048576.0f);
+    return bx == 0 ? KEY_ZERO : key;
 }
 
 __device__ __forceinline__ int greedy_key(double x) {
