@@ -323,19 +323,28 @@ def run_ours(args, ws, rank, local):
     resid = float(np.linalg.norm(p.a @ v_np - v_np * w_np) / np.linalg.norm(p.a))
     orth = float(np.linalg.norm(v_np.T @ v_np - np.eye(n)))
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers.  V comes back as
+    # the transpose view of a row-major array, so it is copied into the
+    # transpose view of the host buffer (one contiguous copy, no device
+    # temporary).  One untimed pass first: the first copies of a process
+    # load their kernels and grow the allocator (about 1 s, once).
     a_host = torch.tensor(p.a).pin_memory()
     w_host = torch.empty(n, dtype=torch.float64).pin_memory()
     v_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        a_dev = a_host.to(dev, non_blocking=True)
+        w_d, v_d, _, _ = solve(mat=a_dev)
+        w_host.copy_(w_d, non_blocking=True)
+        v_host.t().copy_(v_d, non_blocking=True)
+
+    e2e_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_steps = max(1, min(args.steps, 2))
     e0.record(stream)
     for _ in range(e_steps):
-        a_dev = a_host.to(dev, non_blocking=True)
-        w_d, v_d, _, _ = solve(mat=a_dev)
-        w_host.copy_(w_d, non_blocking=True)
-        v_host.copy_(v_d, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1)) / e_steps
