@@ -201,9 +201,11 @@ int pjac_eig_lowprec(pjac_handle* h, const double* A, int n, int lda, float* Q0,
  *     op(B); slice products run on the tensor cores in BF16 with exact FP32
  *     accumulation and are summed exactly in 64-bit fixed point (Ozaki, Ogita,
  *     Oishi and Rump's error-free splitting).  Error per entry at most
- *     |alpha| 2^(e_i+f_j) (k (S+3) 2^(-bS) + 2^-47) + 2^-53 |C_ij|, where
- *     2^(e_i-1) <= max_l |op(A)_il| < 2^e_i, likewise f_j for op(B)'s
- *     column j, and b S = 54 (b = 6, S = 9) or 55 (b = 5, S = 11).
+ *     |alpha| 2^(e_i+f_j) (k (S+3) 2^(-bS) + T 2^-(2b+38)) + 2^-53 |C_ij|,
+ *     where 2^(e_i-1) <= max_l |op(A)_il| < 2^e_i, likewise f_j for op(B)'s
+ *     column j, b S = 54 (b = 6, S = 9) or 55 (b = 5, S = 11), and T = 17
+ *     (b = 6) or 30 (b = 5) slice products are rounded to 37 fractional bits
+ *     in the fixed-point sum.
  *   PJAC_TRANSFORM_FP64: plain FP64 products on the CUDA cores.
  * All matrices are FP64, column-major, in device memory.
  *   transa, transb  0: op(X) = X, 1: op(X) = X^T.

@@ -11,30 +11,36 @@
 //    0 <= tail < 2^-bS.  The entry's sign goes on every digit.  A digit is an
 //    integer of at most 6 bits, exact in BF16.
 //  * The product of slice s of A and slice t of B has integer entries of
-//    magnitude at most K (2^b - 1)^2.  With G K (2^b - 1)^2 <= 2^24 every
-//    partial sum of G such products is an integer below 2^24, so the FP32
-//    accumulator in TMEM adds them without rounding in any order.  Pairs with
-//    the same s + t = d share the scale 2^-b(d+2), so up to G of them share
-//    one accumulator.
+//    magnitude at most K (2^b - 1)^2 <= 2^24, so its FP32 accumulator in
+//    TMEM adds the partial products without rounding in any order.  Pair
+//    (s, t) has the scale 2^-b(s+t+2).
 //  * Pairs with s + t >= S are not formed: together they weigh less than the
-//    digit truncation.  The epilogue adds the groups in 64-bit fixed point,
-//    sum_d P_d 2^(FRAC - bd) with FRAC = 37 fractional bits: every P_d is an
-//    integer, so the sum is exact except for the lowest bits of the last
-//    diagonals (bd > FRAC), which are truncated.  The magnitude stays below
-//    2^24.1 (sum_d (d+1) K (2^b-1)^2 2^-bd), far inside 63 bits.  Then
+//    digit truncation.  The epilogue adds the pairs in 64-bit fixed point,
+//    sum_st P_st 2^(FRAC - b(s+t)) with FRAC = 37 fractional bits: every P_st
+//    is an integer, so the sum is exact except for the pairs of the last
+//    diagonals (b(s+t) > FRAC), each rounded to a multiple of 2^-FRAC on its
+//    own (by at most half a unit): T of them, T = 17 for b = 6 and 30 for
+//    b = 5.  In units of 2^-FRAC the
+//    sum stays below 2^(24.1 + FRAC) = 2^61.1 (sum_d (d+1) K (2^b-1)^2 2^-bd
+//    < 2^24.1), inside 63 bits.  Then
 //    C_ij = alpha 2^(e_i + f_j - 2b - FRAC) fl64(sum)  (+ beta C_ij).
 //  Error bound, u = 2^-53:
-//    |C - alpha op(A)op(B)|_ij <= |alpha| 2^(e_i+f_j) (K (S+3) 2^-bS + 2^-47) + u |C_ij|.
+//    |C - alpha op(A)op(B)|_ij <= |alpha| 2^(e_i+f_j) (K (S+3) 2^-bS + T 2^-(2b+FRAC+1)) + u |C_ij|.
 //
 // Kernels:
 //  tc_rowmax_kernel  max |x| of every row of the two K-major operand views
 //  tc_split_kernel   the digit slices, BF16, K-major, padded to the tiles
-//  tc_gemm_kernel    one 128x128 output tile per CTA; warp 0 issues TMA
-//                    loads (128B-swizzled 128x64 boxes) into a 6-stage ring,
-//                    warp 1 issues tcgen05.mma (M=128, N=128, K=16) into one
-//                    of two TMEM accumulators per group, warps 2..9 read the
-//                    finished accumulator (tcgen05.ld) and add it into 64-bit
-//                    integer registers while the next group accumulates.
+//  tc_gemm_kernel    one 128x128 output tile per CTA.  The pairs are taken in
+//                    units of up to 2 x 2 (slices s0, s0+1 of A times t0, t0+1
+//                    of B): a K block of a unit loads its (at most four)
+//                    operand tiles once and feeds up to four pair products,
+//                    half the shared-memory fill per product of one pair at a
+//                    time.  Warp 0 issues TMA loads (128B-swizzled 128x64
+//                    boxes) into a 3-stage ring, warp 1 issues tcgen05.mma
+//                    (M=128, N=128, K=16) into one 128-column TMEM
+//                    accumulator per pair of the unit, warps 2..9 read the
+//                    finished accumulators (tcgen05.ld) and add them into
+//                    64-bit integer registers.
 //  tc_reduce_kernel  sums the per-split partial tiles (exactly, as integers)
 //                    when one tile is spread over several CTAs, and scales.
 // Every mbarrier wait is bounded: on time-out the CTA records an error in the
@@ -51,22 +57,28 @@ namespace pjac {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 64;  // output tile, K block (64 BF16 = 128 B rows)
-constexpr int STAGES = 6;
-constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = TM * TK * 2;     // one 128 x 64 BF16 operand tile (TM == TN)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES; // A slices s0, s0+1 then B slices t0, t0+1
 constexpr int NTHREADS = 320;               // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int TMEM_COLS = 2 * TN;           // two FP32 accumulators of 128 columns
-constexpr int MAXG = 72, MAXSPLIT = 16;
+constexpr int TMEM_COLS = 4 * TN;           // four FP32 accumulators of 128 columns
+constexpr int MAXU = 40, MAXSPLIT = 16;
 constexpr long long WAIT_CYCLES = 2000000000LL;  // about one second
 constexpr int FRAC = 37;                         // fractional bits of the fixed-point sum
 
 struct TcPlan {
     int Mp, Np, Kp, nkb;  // padded sizes, K blocks
-    int S, b, G;          // slices, bits per digit, pairs per accumulator
-    int ngroups, splits;
-    int group[MAXG];      // d | s0 << 8 | count << 16 : pairs (s, d - s), s0 <= s < s0 + count
+    int S, b;             // slices, bits per digit
+    int nunits, splits;
+    int unit[MAXU];       // s0 | t0 << 8 | ra << 16 | rb << 20: pairs (s0 + a, t0 + c), a < ra, c < rb,
+                          // s0 + a + t0 + c < S
     int split_begin[MAXSPLIT + 1];
 };
+
+__host__ __device__ __forceinline__ bool unit_pair(int u, int S, int a, int c) {
+    const int s0 = u & 255, t0 = (u >> 8) & 255, ra = (u >> 16) & 15, rb = (u >> 20) & 15;
+    return a < ra && c < rb && s0 + a + t0 + c < S;
+}
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -289,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                    const unsigned long long* __restrict__ bmax, int m, int n, double alpha, double beta,
                    double* C, long long ldc, long long* partial, int* err) {
     extern __shared__ unsigned char dsm_raw[];
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], mdone;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull, tempty, mdone;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     unsigned char* base =
@@ -304,10 +316,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 8);
-        }
+        mbar_init(&tfull, 1);
+        mbar_init(&tempty, 8);
         mbar_init(&mdone, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -330,21 +340,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int it = 0;
             bool ok = true;
             for (int g = g0; g < g1 && ok; ++g) {
-                const int gd = P.group[g] & 255, gs = (P.group[g] >> 8) & 255, gc = P.group[g] >> 16;
-                for (int q = 0; q < gc && ok; ++q) {
-                    const int s = gs + q, t = gd - s;
-                    for (int kb = 0; kb < P.nkb; ++kb, ++it) {
-                        const int st = it % STAGES;
-                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                        if (!mbar_wait(&empty[st], ph ^ 1u, abort_v, err, 1)) {
-                            ok = false;
-                            break;
-                        }
-                        unsigned char* sa = base + st * STAGE_BYTES;
-                        mbar_expect_tx(&full[st], STAGE_BYTES);
-                        tma_load_2d(sa, &tmA, &full[st], kb * TK, s * P.Mp + mt * TM);
-                        tma_load_2d(sa + A_BYTES, &tmB, &full[st], kb * TK, t * P.Np + nt * TN);
+                const int u = P.unit[g];
+                const int s0 = u & 255, t0 = (u >> 8) & 255, ra = (u >> 16) & 15, rb = (u >> 20) & 15;
+                for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u, abort_v, err, 1)) {
+                        ok = false;
+                        break;
                     }
+                    unsigned char* sa = base + st * STAGE_BYTES;
+                    mbar_expect_tx(&full[st], (uint32_t)((ra + rb) * TILE_BYTES));
+                    for (int a = 0; a < ra; ++a)
+                        tma_load_2d(sa + a * TILE_BYTES, &tmA, &full[st], kb * TK, (s0 + a) * P.Mp + mt * TM);
+                    for (int c = 0; c < rb; ++c)
+                        tma_load_2d(sa + (2 + c) * TILE_BYTES, &tmB, &full[st], kb * TK, (t0 + c) * P.Np + nt * TN);
                 }
             }
             // the copies of the last STAGES issues may still be in flight after an abort
@@ -356,32 +366,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int it = 0, gi = 0;
             bool ok = true;
             for (int g = g0; g < g1 && ok; ++g, ++gi) {
-                const int buf = gi & 1;
-                if (!mbar_wait(&tempty[buf], ((uint32_t)(gi >> 1) & 1u) ^ 1u, abort_v, err, 2)) break;
+                // the epilogue has read every accumulator of the previous unit
+                if (!mbar_wait(&tempty, ((uint32_t)gi & 1u) ^ 1u, abort_v, err, 2)) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)(buf * TN);
-                const int gc = P.group[g] >> 16;
-                uint32_t acc = 0;
-                for (int q = 0; q < gc && ok; ++q) {
-                    for (int kb = 0; kb < P.nkb; ++kb, ++it) {
-                        const int st = it % STAGES;
-                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                        if (!mbar_wait(&full[st], ph, abort_v, err, 2)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t sa = smem_u32(base + st * STAGE_BYTES);
-                        const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + A_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < TK / 16; ++kk) {  // 16 BF16 = 32 B = 2 descriptor units
-                            tc_mma(dt, da + 2 * kk, db + 2 * kk, IDESC, acc);
-                            acc = 1;
-                        }
-                        tc_commit(&empty[st]);
+                const int u = P.unit[g];
+                for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!mbar_wait(&full[st], ph, abort_v, err, 2)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(base + st * STAGE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk)  // 16 BF16 = 32 B = 2 descriptor units
+#pragma unroll
+                        for (int a = 0; a < 2; ++a)
+#pragma unroll
+                            for (int c = 0; c < 2; ++c)
+                                if (unit_pair(u, P.S, a, c))
+                                    tc_mma(tmem + (uint32_t)((2 * a + c) * TN),
+                                           sw128_desc(sa + a * TILE_BYTES) + 2 * kk,
+                                           sw128_desc(sa + (2 + c) * TILE_BYTES) + 2 * kk, IDESC,
+                                           (kb | kk) != 0);
+                    tc_commit(&empty[st]);
                 }
-                if (ok) tc_commit(&tfull[buf]);
+                if (ok) tc_commit(&tfull);
             }
             tc_commit(&mdone);  // arrives once every MMA issued above has finished
             mbar_drain(&mdone, 0);
@@ -396,31 +407,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         bool ok = true;
         int gi = 0;
         for (int g = g0; g < g1; ++g, ++gi) {
-            const int buf = gi & 1;
             // the decision must be warp-uniform: tcgen05.ld is a whole-warp instruction
-            const bool got = mbar_wait(&tfull[buf], (uint32_t)(gi >> 1) & 1u, abort_v, err, 4);
+            const bool got = mbar_wait(&tfull, (uint32_t)gi & 1u, abort_v, err, 4);
             if (!__all_sync(0xffffffffu, got)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            // weight 2^-bd in units of 2^-FRAC: a left shift, or for the last
-            // diagonals a right shift that drops bits below 2^-FRAC
-            const int sh = FRAC - P.b * (P.group[g] & 255);
-            const int ls = sh > 0 ? sh : 0, rs = sh < 0 ? -sh : 0;
-            const uint32_t ta = tmem + (uint32_t)(buf * TN + hcol * 64) + ((uint32_t)(q * 32) << 16);
+            const int u = P.unit[g];
+            const int d0 = (u & 255) + ((u >> 8) & 255);
+#pragma unroll 1
+            for (int pc = 0; pc < 4; ++pc) {
+                const int a = pc >> 1, c2 = pc & 1;
+                if (!unit_pair(u, P.S, a, c2)) continue;
+                // weight 2^-b(s+t) in units of 2^-FRAC: a left shift, or for
+                // the last diagonals a right shift that rounds to the
+                // nearest unit (ties up), so that the T roundings do not
+                // all lean one way
+                const int sh = FRAC - P.b * (d0 + a + c2);
+                const int ls = sh > 0 ? sh : 0, rs = sh < 0 ? -sh : 0;
+                const int rnd = rs > 0 ? 1 << (rs - 1) : 0;
+                const uint32_t ta = tmem + (uint32_t)(pc * TN + hcol * 64) + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch) {
-                uint32_t v[32];
-                tmem_ld32(ta + ch * 32, v);
-                // v is an integer of magnitude <= 2^24: the conversion is exact
+                for (int ch = 0; ch < 2; ++ch) {
+                    uint32_t v[32];
+                    tmem_ld32(ta + ch * 32, v);
+                    // v is an integer of magnitude <= 2^24: the conversion is exact
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    acc[ch * 32 + c] += (long long)(__float2int_rn(__uint_as_float(v[c])) >> rs) << ls;
+                    for (int c = 0; c < 32; ++c)
+                        acc[ch * 32 + c] += (long long)((__float2int_rn(__uint_as_float(v[c])) + rnd) >> rs) << ls;
+                }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
+            if (lane == 0) mbar_arrive(&tempty);
         }
         if (ok && !*abort_v) {
             const int i = mt * TM + row;
@@ -489,7 +509,7 @@ int device_sms() {
     return sms > 0 ? sms : 148;
 }
 
-// Contiguous ranges of groups with about npairs / splits pairs each (every
+// Contiguous ranges of units with about npairs / splits pairs each (every
 // range non-empty).  Returns the largest pair count of a range.
 int split_groups(const int* cnt, int ng, int npairs, int splits, int* sb) {
     sb[0] = 0;
@@ -513,8 +533,9 @@ int split_groups(const int* cnt, int ng, int npairs, int splits, int* sb) {
     return maxp;
 }
 
-// Digit width b, slice count S and accumulator sharing G for inner dimension k;
-// false when k is too large for exact FP32 accumulation of one product.
+// Digit width b, slice count S and the units of slice pairs for inner
+// dimension k; false when k is too large for exact FP32 accumulation of one
+// product.
 bool make_layout(int m, int n, int k, int sms, Layout& L) {
     if (m < 1 || n < 1 || k < 1) return false;
     TcPlan& P = L.P;
@@ -526,33 +547,34 @@ bool make_layout(int m, int n, int k, int sms, Layout& L) {
     const double dmax = (double)((1 << b) - 1);
     P.b = b;
     P.S = (54 + b - 1) / b;
-    P.G = (int)(lim / ((double)k * dmax * dmax));
-    if (P.G > P.S) P.G = P.S;
+    (void)dmax;
     P.Mp = (m + TM - 1) / TM * TM;
     P.Np = (n + TN - 1) / TN * TN;
     P.Kp = (k + TK - 1) / TK * TK;
     P.nkb = P.Kp / TK;
+    // the 2 x 2 blocks (s0, t0 even) of the triangle s + t < S; a block at
+    // the edge keeps the rows and columns that hold a pair
     int ng = 0, npairs = 0;
-    int cnt[MAXG];
-    for (int d = 0; d < P.S; ++d) {
-        const int np = d + 1, chunks = (np + P.G - 1) / P.G;
-        int s0 = 0;
-        for (int c = 0; c < chunks; ++c) {
-            const int sz = np / chunks + (c < np % chunks ? 1 : 0);
-            if (ng >= MAXG) return false;
-            P.group[ng] = d | (s0 << 8) | (sz << 16);
-            cnt[ng++] = sz;
-            s0 += sz;
-            npairs += sz;
+    int cnt[MAXU];
+    for (int s0 = 0; s0 < P.S; s0 += 2)
+        for (int t0 = 0; s0 + t0 < P.S; t0 += 2) {
+            const int ra = s0 + 1 + t0 < P.S ? 2 : 1, rb = s0 + t0 + 1 < P.S ? 2 : 1;
+            if (ng >= MAXU) return false;
+            const int u = s0 | (t0 << 8) | (ra << 16) | (rb << 20);
+            int np = 0;
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c) np += unit_pair(u, P.S, a, c) ? 1 : 0;
+            P.unit[ng] = u;
+            cnt[ng++] = np;
+            npairs += np;
         }
-    }
-    P.ngroups = ng;
-    // Spread the groups of one output tile over `splits` CTAs when there are
+    P.nunits = ng;
+    // Spread the units of one output tile over `splits` CTAs when there are
     // too few tiles to fill the GPU evenly.  Model (seconds): waves of CTAs x
     // (largest pair count of a split x time per slice pair + fixed CTA cost),
     // plus the reduction's HBM traffic when splits > 1.
     const int tiles = (P.Mp / TM) * (P.Np / TN);
-    const double t_pair = (double)P.nkb * 664.0 / 1.9e9;   // 4 MMAs per K block at half the peak rate
+    const double t_pair = ((double)P.nkb * 4.0 * 64.0 / 0.7 + 1100.0) / 1.9e9;   // 4 MMAs per K block, drain
     double best = 1e30;
     int smax = ng < MAXSPLIT ? ng : MAXSPLIT;
     int bsplit[MAXSPLIT + 1];

@@ -12,7 +12,7 @@ Two kinds of checks:
   * accuracy: on dense inputs (normal entries, rows scaled by powers of two
     up to 2^+-30, and a case with a 2^+-8 spread inside every row) the error
     against a double-double product stays within the bound of the splitting,
-    |C - AB|_ij <= 2^(e_i + f_j) (k (S+3) 2^-bS + 2^-47) + u |C|, over ragged shapes,
+    |C - AB|_ij <= 2^(e_i + f_j) (k (S+3) 2^-bS + T 2^-(2b+38)) + u |C|, over ragged shapes,
     both transposes, alpha and beta, k at the b = 6 limit and beyond it
     (b = 5).
 """
@@ -69,7 +69,10 @@ def bound(a_op, b_op, alpha=1.0):
     eb = exp_above(np.abs(b_op).max(axis=0))
     scale = np.ldexp(1.0, ea[:, None] + eb[None, :])
     c = np.abs(alpha * (a_op @ b_op))
-    return abs(alpha) * scale * (k * (S + 3) * 2.0 ** (-b * S) + 2.0 ** -47) + 2.0 ** -53 * c
+    # T slice products (s, t) with b (s + t) > 37 are rounded to 37
+    # fractional bits in the fixed-point sum, each by at most half a unit
+    T = sum(d + 1 for d in range(S) if b * d > 37)
+    return abs(alpha) * scale * (k * (S + 3) * 2.0 ** (-b * S) + T * 2.0 ** -(2 * b + 38)) + 2.0 ** -53 * c
 
 
 def two_digit_matrix(rng, rows, cols, maxdigits=False):
