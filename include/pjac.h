@@ -223,6 +223,23 @@ int pjac_product(pjac_handle* h, int transa, int transb, int m, int n, int k, do
                  void* stream);
 
 /*
+ * The products of Sec. 2.1 whose exact value is symmetric: X^T X in the
+ * Newton--Schulz steps and X^T (A X) in the transform (n x n results).
+ * Same arguments as pjac_product with m = n; the caller states that
+ * op(A) op(B) is symmetric in exact arithmetic.  With the split product only
+ * the 128 x 128 output tiles on and above the diagonal are computed and
+ * entry (i, j), i <= j, is written to both (i, j) and (j, i): about half the
+ * work, and C is exactly symmetric.  Each written pair carries the error
+ * bound of pjac_product for entry (i, j).  With PJAC_TRANSFORM_FP64 the full
+ * product is formed and then averaged with its transpose.  beta != 0 uses
+ * C(i, j) and C(j, i) each for its own entry.
+ * Synchronises the stream.  Errors as pjac_product.
+ */
+int pjac_product_symmetric(pjac_handle* h, int transa, int transb, int n, int k, double alpha,
+                           const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                           void* stream);
+
+/*
  * Full solve: preconditioner, then Algorithm 1 on A1 with V0 = Q, then the
  * readout (W ascending, V's columns in the same order).
  *   A   [in]  n x n symmetric, not modified.

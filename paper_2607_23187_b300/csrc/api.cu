@@ -263,12 +263,16 @@ static int tc_status(pjac_handle* h, cudaStream_t st) {
 
 // C = alpha op(A) op(B) + beta C with the product chosen by the options
 // (the split-BF16 workspace was prepared by tc_prepare for this shape).
+// sym (m == n): the caller knows op(A) op(B) to be symmetric in exact
+// arithmetic; C comes out exactly symmetric (the split product computes the
+// tiles on and above the diagonal and mirrors them, the FP64 product is
+// symmetrised).
 static int product_mnk(pjac_handle* h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
                        long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool sym = false) {
     if (h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16) {
         cudaError_t e = gemm_split_bf16(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, h->tcws.p,
-                                        h->tcws.bytes, st);
+                                        h->tcws.bytes, st, sym);
         if (e == cudaErrorNotSupported) {
             cudaGetLastError();
             return set_err(PJAC_ENOTIMPL, "split-BF16 tensor-core product not available for this shape");
@@ -277,6 +281,7 @@ static int product_mnk(pjac_handle* h, bool ta, bool tb, int m, int n, int k, do
         return PJAC_OK;
     }
     CK(gemm_f64(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st));
+    if (sym) CK(symmetrize(C, ldc, n, st));
     return PJAC_OK;
 }
 
@@ -285,12 +290,18 @@ static int product(pjac_handle* h, bool ta, bool tb, int n, double alpha, const 
     return product_mnk(h, ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
+// A product whose exact value is symmetric (X^T X, X^T (S X) with S symmetric).
+static int product_sym(pjac_handle* h, bool ta, bool tb, int n, double alpha, const double* A, long long lda,
+                       const double* B, long long ldb, double beta, double* C, long long ldc, cudaStream_t st) {
+    return product_mnk(h, ta, tb, n, n, n, alpha, A, lda, B, ldb, beta, C, ldc, st, true);
+}
+
 // X <- X (3I - X^T X) / 2, steps times (Newton--Schulz; Sec. 2.1 names it
 // as one way to restore orthogonality to working precision).
 static int newton_schulz(pjac_handle* h, double* Q, long long ldq, int n, int steps, SolveWs& w,
                          cudaStream_t st) {
     for (int it = 0; it < steps; ++it) {
-        int r = product(h, true, false, n, 1.0, Q, ldq, Q, ldq, 0.0, w.Y, n, st);
+        int r = product_sym(h, true, false, n, 1.0, Q, ldq, Q, ldq, 0.0, w.Y, n, st);
         if (r) return r;
         CK(three_i_minus(w.Y, n, n, st));
         r = product(h, false, false, n, 0.5, Q, ldq, w.Y, n, 0.0, w.T, n, st);
@@ -319,9 +330,8 @@ static int lowprec_basis(pjac_handle* h, const double* A, int n, long long lda, 
     CK(round_to_fp32(A, lda, w.Y, n, n, st));                             // Y = fl32(A)
     r = product(h, false, false, n, 1.0, w.Y, n, Q, ldq, 0.0, w.T, n, st);    // T = fl32(A) X
     if (r) return r;
-    r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st);     // B = X^T T
+    r = product_sym(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, w.Y, n, st); // B = X^T T, symmetric
     if (r) return r;
-    CK(symmetrize(w.Y, n, n, st));
     const int rsw = h->opts.fp32_sweeps > 0 && h->opts.fp32_sweeps < 20 ? h->opts.fp32_sweeps : 20;
     CK(refine_fp32(w.Y, n, w.Q0, w.d32, rsw, h->coop_cap, st));                        // D
     CK(copy_f32_to_f64(w.Q0, n, w.T, n, n, st));
@@ -368,7 +378,7 @@ static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, lo
     h->ref_ns += ns;
     int r;
     for (int it = 0; it < ns; ++it) {
-        r = product(h, true, false, n, 1.0, E, n, E, n, 0.0, w.Y, n, st);         // Y = E^T E
+        r = product_sym(h, true, false, n, 1.0, E, n, E, n, 0.0, w.Y, n, st);     // Y = E^T E
         if (r) return r;
         CK(refine_r(w.Y, E, n, st));                                               // R = Y + E + E^T
         r = product(h, false, false, n, -0.5, E, n, w.Y, n, 0.0, w.T, n, st);     // T = -E R / 2
@@ -377,7 +387,7 @@ static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, lo
     }
     r = product(h, false, false, n, 1.0, A1, lda1, E, n, 0.0, w.T, n, st);       // T = A1 E
     if (r) return r;
-    r = product(h, true, false, n, 1.0, E, n, w.T, n, 0.0, w.Y, n, st);          // Y = E^T T
+    r = product_sym(h, true, false, n, 1.0, E, n, w.T, n, 0.0, w.Y, n, st);      // Y = E^T A1 E
     if (r) return r;
     CK(refine_a1(A1, lda1, w.T, w.Y, n, st));
     CK(symmetrize(A1, lda1, n, st));
@@ -408,9 +418,8 @@ static int precondition_ws(pjac_handle* h, const double* A, int n, long long lda
     // A1 = Q^T (A Q), symmetrised
     r = product(h, false, false, n, 1.0, A, lda, Q, ldq, 0.0, w.T, n, st);
     if (r) return r;
-    r = product(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
+    r = product_sym(h, true, false, n, 1.0, Q, ldq, w.T, n, 0.0, A1, lda1, st);
     if (r) return r;
-    CK(symmetrize(A1, lda1, n, st));
     h->ref_n = n;
     h->ref_done = h->ref_ns = 0;
     for (int k = 0; k < h->opts.refine_steps; ++k) {
@@ -479,6 +488,25 @@ extern "C" int pjac_product(pjac_handle* h, int transa, int transb, int m, int n
     int r = tc_prepare(h, m, n, k, st);
     if (r) return r;
     r = product_mnk(h, transa != 0, transb != 0, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    if (r) return r;
+    return tc_status(h, st);
+}
+
+extern "C" int pjac_product_symmetric(pjac_handle* h, int transa, int transb, int n, int k, double alpha,
+                                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                                      int ldc, void* stream) {
+    if (!h || !A || !B || !C) return set_err(PJAC_EINVAL, "NULL argument");
+    if (n < 1 || k < 1 || n > PJAC_MAX_N || k > PJAC_MAX_N)
+        return set_err(PJAC_EINVAL, "n, k = %d, %d out of range [1, %d]", n, k, PJAC_MAX_N);
+    if ((transa != 0 && transa != 1) || (transb != 0 && transb != 1))
+        return set_err(PJAC_EINVAL, "transa and transb must be 0 or 1");
+    if (lda < (transa ? k : n) || ldb < (transb ? n : k) || ldc < n)
+        return set_err(PJAC_EINVAL, "leading dimension too small");
+    std::lock_guard<std::mutex> lk(h->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = tc_prepare(h, n, n, k, st);
+    if (r) return r;
+    r = product_mnk(h, transa != 0, transb != 0, n, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st, true);
     if (r) return r;
     return tc_status(h, st);
 }
@@ -816,20 +844,22 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
     if (h->opts.no_precondition) return 6;
     const bool split = h->opts.transform == PJAC_TRANSFORM_SPLIT_BF16;
     const int P = split ? gemm_split_bf16_launches(n, n, n) : 1;   // launches per product
+    // launches per symmetric product (the FP64 product is symmetrised after)
+    const int Ps = split ? gemm_split_bf16_launches(n, n, n, true) : 2;
     const int ns = h->opts.ns_steps;
     // input check, FP32 diagonaliser, copy to FP64
     int c = 3;
     // Newton--Schulz before the refinement (2 steps) and after it (ns steps):
-    // two products, 3I - Y and a copy per step
-    c += (2 + ns) * (2 * P + 2);
-    // fl32(A), T = fl32(A) X, B = X^T T, symmetrise, refinement, copy, X D, add
-    c += 1 + 2 * P + 1 + 1 + 1 + P + 1;
-    // transform (two products) and symmetrise, Jacobi, readout (two kernels)
-    c += 2 * P + 1 + 1 + 2;
+    // two products (one symmetric), 3I - Y and a copy per step
+    c += (2 + ns) * (P + Ps + 2);
+    // fl32(A), T = fl32(A) X, B = X^T T (symmetric), refinement, copy, X D, add
+    c += 1 + P + Ps + 1 + 1 + P + 1;
+    // transform (two products, one symmetric), Jacobi, readout (two kernels)
+    c += P + Ps + 1 + 2;
     // refinement steps: build and scale (every step), then for the steps
-    // with a nonzero correction its Newton--Schulz steps (two products and
-    // two element-wise steps each), three products, the A1 update,
-    // symmetrise, the Q update.  The Newton--Schulz count depends on the
+    // with a nonzero correction its Newton--Schulz steps (two products, one
+    // symmetric, and two element-wise steps each), three products (one
+    // symmetric), the A1 update, symmetrise, the Q update.  The Newton--Schulz count depends on the
     // correction's size: the handle's last solve of this order gives it,
     // else the largest count is assumed.
     if (h->opts.refine_steps > 0) {
@@ -838,7 +868,7 @@ extern "C" int pjac_solve_launch_count(pjac_handle* h, int n) {
             done = h->ref_done;
             nss = h->ref_ns;
         }
-        c += 2 * h->opts.refine_steps + nss * (2 * P + 2) + done * (3 * P + 3);
+        c += 2 * h->opts.refine_steps + nss * (P + Ps + 2) + done * (2 * P + Ps + 3);
     }
     if (split) c += 1;  // product status folded into the solve record
     return c;

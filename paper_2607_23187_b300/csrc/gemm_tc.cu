@@ -63,6 +63,7 @@ constexpr int STAGE_BYTES = 4 * TILE_BYTES; // A slices s0, s0+1 then B slices t
 constexpr int NTHREADS = 320;               // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int TMEM_COLS = 4 * TN;           // four FP32 accumulators of 128 columns
 constexpr int MAXU = 40, MAXSPLIT = 16;
+constexpr int RASTER_M = 12;                // row tiles per raster group
 constexpr long long WAIT_CYCLES = 2000000000LL;  // about one second
 constexpr int FRAC = 37;                         // fractional bits of the fixed-point sum
 
@@ -70,10 +71,20 @@ struct TcPlan {
     int Mp, Np, Kp, nkb;  // padded sizes, K blocks
     int S, b;             // slices, bits per digit
     int nunits, splits;
+    int sym;              // symmetric product: tiles on and above the diagonal only, mirrored
     int unit[MAXU];       // s0 | t0 << 8 | ra << 16 | rb << 20: pairs (s0 + a, t0 + c), a < ra, c < rb,
                           // s0 + a + t0 + c < S
     int split_begin[MAXSPLIT + 1];
 };
+
+// Tile (mt, nt), mt <= nt, of linear index t = nt (nt + 1) / 2 + mt.
+__host__ __device__ __forceinline__ void sym_tile(int t, int& mt, int& nt) {
+    int c = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (c * (c + 1) / 2 > t) --c;
+    while ((c + 1) * (c + 2) / 2 <= t) ++c;
+    nt = c;
+    mt = t - c * (c + 1) / 2;
+}
 
 __host__ __device__ __forceinline__ bool unit_pair(int u, int S, int a, int c) {
     const int s0 = u & 255, t0 = (u >> 8) & 255, ra = (u >> 16) & 15, rb = (u >> 20) & 15;
@@ -307,7 +318,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+    // Output tile of the linear index blockIdx.x: groups of RASTER_M row
+    // tiles, row tile fastest inside a group, so that the CTAs resident at
+    // one time cover a square-ish block of the output and find the slice
+    // tiles of A and B that their neighbours load in L2.  A symmetric
+    // product takes the tiles mt <= nt, column by column.
+    int mt, nt;
+    if (P.sym) {
+        sym_tile(blockIdx.x, mt, nt);
+    } else {
+        const int tn_all = P.Np / TN;
+        const int grp = blockIdx.x / (RASTER_M * tn_all), rem = blockIdx.x % (RASTER_M * tn_all);
+        const int m0 = grp * RASTER_M, gm = min(RASTER_M, P.Mp / TM - m0);
+        mt = m0 + rem % gm;
+        nt = rem / gm;
+    }
+    const int z = blockIdx.z;
     const int g0 = P.split_begin[z], g1 = P.split_begin[z + 1];
     volatile int* abort_v = &abort_flag;
 
@@ -451,11 +477,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int c = 0; c < 64; ++c) {
                         const int j = j0 + c;
-                        if (j < n) {
-                            double r = alpha * times_pow2((double)acc[c], ea + exp_above(bmax[j]));
+                        // symmetric: entry (i, j), i <= j, also goes to (j, i)
+                        if (j < n && (!P.sym || i <= j)) {
+                            const double r0 = alpha * times_pow2((double)acc[c], ea + exp_above(bmax[j]));
                             double* cp = C + i + (long long)j * ldc;
-                            if (beta != 0.0) r = __fma_rn(beta, *cp, r);
-                            *cp = r;
+                            *cp = beta != 0.0 ? __fma_rn(beta, *cp, r0) : r0;
+                            if (P.sym && i != j) {
+                                double* cq = C + j + (long long)i * ldc;
+                                *cq = beta != 0.0 ? __fma_rn(beta, *cq, r0) : r0;
+                            }
                         }
                     }
                 }
@@ -479,17 +509,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 __global__ void tc_reduce_kernel(const long long* __restrict__ part, int splits, int Mp, int Np, int m, int n,
                                  int shift, const unsigned long long* __restrict__ amax,
                                  const unsigned long long* __restrict__ bmax, double alpha, double beta,
-                                 double* C, long long ldc) {
+                                 double* C, long long ldc, int sym) {
     const long long tot = (long long)m * n;
     const long long plane = (long long)Mp * Np;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % m), j = (int)(e / m);
+        const int ie = (int)(e % m), je = (int)(e / m);
+        // symmetric: every entry takes the value computed at (min, max)
+        const int i = sym ? min(ie, je) : ie, j = sym ? max(ie, je) : je;
         const long long* p = part + i + (long long)j * Mp;
         long long s = 0;
         for (int z = 0; z < splits; ++z) s += p[z * plane];
         double r = alpha * times_pow2((double)s, exp_above(amax[i]) + exp_above(bmax[j]) - shift);
-        double* cp = C + i + (long long)j * ldc;
+        double* cp = C + ie + (long long)je * ldc;
         if (beta != 0.0) r = __fma_rn(beta, *cp, r);
         *cp = r;
     }
@@ -536,8 +568,8 @@ int split_groups(const int* cnt, int ng, int npairs, int splits, int* sb) {
 // Digit width b, slice count S and the units of slice pairs for inner
 // dimension k; false when k is too large for exact FP32 accumulation of one
 // product.
-bool make_layout(int m, int n, int k, int sms, Layout& L) {
-    if (m < 1 || n < 1 || k < 1) return false;
+bool make_layout(int m, int n, int k, int sms, Layout& L, bool sym = false) {
+    if (m < 1 || n < 1 || k < 1 || (sym && m != n)) return false;
     TcPlan& P = L.P;
     memset(&P, 0, sizeof(P));
     const double lim = 16777216.0;  // 2^24
@@ -573,7 +605,8 @@ bool make_layout(int m, int n, int k, int sms, Layout& L) {
     // too few tiles to fill the GPU evenly.  Model (seconds): waves of CTAs x
     // (largest pair count of a split x time per slice pair + fixed CTA cost),
     // plus the reduction's HBM traffic when splits > 1.
-    const int tiles = (P.Mp / TM) * (P.Np / TN);
+    P.sym = sym ? 1 : 0;
+    const int tiles = sym ? (P.Np / TN) * (P.Np / TN + 1) / 2 : (P.Mp / TM) * (P.Np / TN);
     const double t_pair = ((double)P.nkb * 4.0 * 64.0 / 0.7 + 1100.0) / 1.9e9;   // 4 MMAs per K block, drain
     double best = 1e30;
     int smax = ng < MAXSPLIT ? ng : MAXSPLIT;
@@ -643,19 +676,24 @@ constexpr int DSMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 
 }  // namespace
 
+// Workspace of either form (a symmetric product may split its tiles
+// differently).
 size_t gemm_split_bf16_ws(int m, int n, int k) {
     Layout L;
     if (!make_layout(m, n, k, device_sms(), L)) return 0;
-    return L.total;
+    size_t total = L.total;
+    Layout Ls;
+    if (m == n && make_layout(m, n, k, device_sms(), Ls, true) && Ls.total > total) total = Ls.total;
+    return total;
 }
 
 int* gemm_split_bf16_errflag(void* ws) { return static_cast<int*>(ws); }
 
 cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha, const double* A, long long lda,
                             const double* B, long long ldb, double beta, double* C, long long ldc, void* ws,
-                            size_t ws_bytes, cudaStream_t st) {
+                            size_t ws_bytes, cudaStream_t st, bool sym) {
     Layout L;
-    if (!make_layout(m, n, k, device_sms(), L) || ws_bytes < L.total) return cudaErrorNotSupported;
+    if (!make_layout(m, n, k, device_sms(), L, sym) || ws_bytes < L.total) return cudaErrorNotSupported;
     const TcPlan& P = L.P;
     char* w = static_cast<char*>(ws);
     unsigned long long* amax = reinterpret_cast<unsigned long long*>(w + L.off_amax);
@@ -691,7 +729,8 @@ cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha,
         attr_err = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, DSMEM_BYTES);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    dim3 grid(P.Mp / TM, P.Np / TN, P.splits);
+    const int tiles = P.sym ? (P.Np / TN) * (P.Np / TN + 1) / 2 : (P.Mp / TM) * (P.Np / TN);
+    dim3 grid(tiles, 1, P.splits);
     tc_gemm_kernel<<<grid, NTHREADS, DSMEM_BYTES, st>>>(mA, mB, P, amax, bmax, m, n, alpha, beta, C, ldc, part,
                                                        err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -700,7 +739,7 @@ cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha,
         int blocks = (int)((tot + 255) / 256);
         if (blocks > 4 * 148 * 8) blocks = 4 * 148 * 8;
         tc_reduce_kernel<<<blocks, 256, 0, st>>>(part, P.splits, P.Mp, P.Np, m, n, 2 * P.b + FRAC, amax, bmax,
-                                                 alpha, beta, C, ldc);
+                                                 alpha, beta, C, ldc, P.sym);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -716,9 +755,9 @@ cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st
 }
 
 // Number of kernel launches one product makes (for launch accounting).
-int gemm_split_bf16_launches(int m, int n, int k) {
+int gemm_split_bf16_launches(int m, int n, int k, bool sym) {
     Layout L;
-    if (!make_layout(m, n, k, device_sms(), L)) return 0;
+    if (!make_layout(m, n, k, device_sms(), L, sym)) return 0;
     return 3 + (L.P.splits > 1 ? 1 : 0);
 }
 

@@ -98,12 +98,15 @@ cudaError_t three_i_minus(double* Y, long long ldy, int n, cudaStream_t st);
 cudaError_t check_finite(const double* A, long long lda, int n, int* d_flag, cudaStream_t st);
 
 // Split-precision products on the tensor cores (BF16 slices, FP32 accumulation).
+// sym (m == n, op(A) op(B) symmetric in exact arithmetic): only the tiles on
+// and above the diagonal are computed; entry (i, j), i <= j, is written to
+// (i, j) and (j, i), so C comes out exactly symmetric.
 cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
                             long long lda, const double* B, long long ldb, double beta, double* C,
-                            long long ldc, void* ws, size_t ws_bytes, cudaStream_t st);
+                            long long ldc, void* ws, size_t ws_bytes, cudaStream_t st, bool sym = false);
 size_t gemm_split_bf16_ws(int m, int n, int k);          // 0: k too large for the exact split product
 int* gemm_split_bf16_errflag(void* ws);                 // device status word (0 = ok), sticky until cleared
-int gemm_split_bf16_launches(int m, int n, int k);      // kernel launches per product
+int gemm_split_bf16_launches(int m, int n, int k, bool sym = false);   // kernel launches per product
 cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st);
 
 // diag32.cu: FP32 parallel-order Jacobi diagonalisation of fl32(A); Q0 out (ld n)

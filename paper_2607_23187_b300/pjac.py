@@ -32,7 +32,8 @@ EXPORTS = (
     "pjac_solve", "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_default_opts",
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
-    "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_solve_launch_count",
+    "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_product_symmetric",
+    "pjac_solve_launch_count",
     "pjac_product_launch_count", "pjac_eig_lowprec", "pjac_svd", "pjac_svd_onesided", "pjac_probe_fp64",
     "pjac_batched_stage_ms", "pjac_batched_tuning", "pjac_fp32_sweeps_done",
 )
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_solve_preconditioned.argtypes = [vp, vp, i, i, vp, i, i, d, vp, vp, i,
                                                 ctypes.POINTER(Info), vp]
         L.pjac_product.argtypes = [vp, i, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]
+        L.pjac_product_symmetric.argtypes = [vp, i, i, i, i, d, vp, i, vp, i, d, vp, i, vp]
         L.pjac_eig_lowprec.argtypes = [vp, vp, i, i, vp, i, vp]
         L.pjac_svd.argtypes = [vp, vp, i, i, i, vp, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
         L.pjac_svd_onesided.argtypes = [vp, vp, i, i, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
@@ -260,6 +262,32 @@ def pjac_product(h: Handle, a: torch.Tensor, b: torch.Tensor, trans_a: bool = Fa
         raise ValueError("c must be a contiguous (m, n) tensor")
     _check(load().pjac_product(h.h, 1 if trans_b else 0, 1 if trans_a else 0, n, m, k, float(alpha),
                                _ptr(b), b.shape[1], _ptr(a), a.shape[1], float(beta), _ptr(c), n, _stream()))
+    return c
+
+
+def pjac_product_symmetric(h: Handle, a: torch.Tensor, b: torch.Tensor, trans_a: bool = False,
+                           trans_b: bool = False, alpha: float = 1.0, beta: float = 0.0,
+                           c: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """alpha op(a) @ op(b) + beta c for a product the caller knows to be
+    symmetric in exact arithmetic; the result is exactly symmetric.  As in
+    pjac_product the library is handed C^T = op(b)^T op(a)^T (also
+    symmetric)."""
+    a = a.contiguous()
+    b = b.contiguous()
+    m = a.shape[1] if trans_a else a.shape[0]
+    k = a.shape[0] if trans_a else a.shape[1]
+    kb = b.shape[1] if trans_b else b.shape[0]
+    n = b.shape[0] if trans_b else b.shape[1]
+    if kb != k or m != n:
+        raise ValueError(f"expected op(a) {m}x{k} and op(b) {kb}x{n} with a square product")
+    if c is None:
+        c = torch.zeros((n, n), dtype=torch.float64, device=a.device)
+        beta = 0.0
+    elif c.shape != (n, n) or not c.is_contiguous():
+        raise ValueError("c must be a contiguous (n, n) tensor")
+    _check(load().pjac_product_symmetric(h.h, 1 if trans_b else 0, 1 if trans_a else 0, n, k, float(alpha),
+                                         _ptr(b), b.shape[1], _ptr(a), a.shape[1], float(beta), _ptr(c), n,
+                                         _stream()))
     return c
 
 

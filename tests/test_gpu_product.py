@@ -142,6 +142,61 @@ def test_transposes_alpha_beta(pj, h, ta, tb):
     assert np.all(np.abs(got - ref) <= tol)
 
 
+def gpu_product_sym(pj, h, a, b, ta=False, tb=False, alpha=1.0, beta=0.0, c=None):
+    A = torch.tensor(np.ascontiguousarray(a), device="cuda")
+    B = torch.tensor(np.ascontiguousarray(b), device="cuda")
+    C = None if c is None else torch.tensor(np.ascontiguousarray(c), device="cuda")
+    out = pj.pjac_product_symmetric(h, A, B, ta, tb, alpha, beta, C)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,k,form", [(300, 200, "gram"), (130, 7, "gram"), (700, 4100, "gram"),
+                                      (520, 300, "sandwich"), (1024, 1024, "outer")])
+def test_symmetric_product(pj, h, n, k, form):
+    """pjac_product_symmetric (the tiles on and above the diagonal, mirrored):
+    the result is exactly symmetric and every entry is within the bound of
+    the splitting at the entry, (i, j) or (j, i), that was computed.  Cases:
+    Gram matrices X^T X (one with k at the b = 5 digit width, one small
+    enough to spread tiles over several CTAs), X^T (S X) with S symmetric and
+    S X exact (small integers), and X X^T with alpha and beta."""
+    rng = np.random.default_rng(n + 7 * k)
+    alpha, beta, c0 = 1.0, 0.0, None
+    if form == "sandwich":
+        x = rng.integers(-1000, 1000, size=(k, n)).astype(np.float64)
+        s = rng.integers(-50, 50, size=(k, k)).astype(np.float64)
+        s = s + s.T
+        a_op, b_op = x.T, s @ x            # exact: integers below 2^36
+        a_st, b_st, ta, tb = x, s @ x, True, False
+    else:
+        x = rng.standard_normal((k, n)) * np.ldexp(1.0, rng.integers(-20, 20, size=(1, n)))
+        if form == "gram":
+            a_op, b_op = x.T, x
+            a_st, b_st, ta, tb = x, x, True, False
+        else:
+            x = x.T.copy()                 # n x k, C = X X^T
+            a_op, b_op = x, x.T
+            a_st, b_st, ta, tb = x, x, False, True
+            alpha, beta = 0.5, -1.5
+            c0 = rng.standard_normal((n, n))
+            c0 = c0 + c0.T
+    got = gpu_product_sym(pj, h, a_st, b_st, ta, tb, alpha, beta, c0)
+    assert np.array_equal(got, got.T)
+    hi, lo = oracle.exact_matmul(a_op, b_op)
+    bnd = bound(a_op, b_op, alpha)
+    tol = np.maximum(bnd, bnd.T)
+    if c0 is None:
+        err = np.abs((got - alpha * hi) - alpha * lo)
+    else:
+        ref = alpha * hi + beta * c0
+        err = np.abs(got - ref)
+        tol = tol + 2 * 2.0 ** -53 * (np.abs(alpha * hi) + np.abs(beta * c0))
+    assert np.all(err <= tol), float((err / tol).max())
+    with pj.Handle(transform="fp64") as h64:
+        g64 = gpu_product_sym(pj, h64, a_st, b_st, ta, tb, alpha, beta, c0)
+    assert np.array_equal(g64, g64.T)
+
+
 def test_fp64_option_matches_plain_product(pj):
     """The same entry point with the FP64 option is the CUDA-core product."""
     rng = np.random.default_rng(5)
@@ -160,6 +215,9 @@ def test_bad_arguments(pj, h):
     assert lib.pjac_product(h.h, 2, 0, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
     assert lib.pjac_product(h.h, 0, 0, 4, 4, 4, 1.0, p, 3, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
     assert lib.pjac_product(h.h, 0, 0, 4, 4, 4, 1.0, None, 4, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
+    assert lib.pjac_product_symmetric(h.h, 0, 0, 0, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
+    assert lib.pjac_product_symmetric(h.h, 0, 2, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None) == pj.PJAC_EINVAL
+    assert lib.pjac_product_symmetric(h.h, 0, 0, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 3, None) == pj.PJAC_EINVAL
 
 
 def test_launch_count(pj, h):

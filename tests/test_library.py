@@ -86,6 +86,7 @@ def test_arguments_rejected_before_any_device_work(lib):
     assert lib.pjac_solve_preconditioned(None, fake, 4, 4, None, 4, 0, 1e-15, fake, None, 4, None, None) == EINVAL
     assert lib.pjac_solve_batched(None, 1, None, None, None, None, None, None, None, 0, 1e-15, None, None) == EINVAL
     assert lib.pjac_product(None, 0, 0, 4, 4, 4, 1.0, fake, 4, fake, 4, 0.0, fake, 4, None) == EINVAL
+    assert lib.pjac_product_symmetric(None, 0, 0, 4, 4, 1.0, fake, 4, fake, 4, 0.0, fake, 4, None) == EINVAL
     noalloc = lib.pjac_solve_preconditioned_noalloc
     assert noalloc(None, 4, 4, None, 4, 0, d1, fake, None, 4, None, None) == EINVAL
     assert noalloc(fake, 0, 4, None, 4, 0, d1, fake, None, 4, None, None) == EINVAL
