@@ -82,6 +82,7 @@ struct Sh {
     double cs[48][2];       // (c, s) of every published candidate (3 per cluster rank)
     double old_di, old_dj;  // diagonal entries before the pending rotation
     double normf, thr, eps_li, scale;
+    int scaled_sum;                // off-diagonal sums scale every entry (extreme ||A1||_F only)
     int pi, pj, nresc, decision;
     int win, pad4;          // inbox index of the pending pivot
     int key_eps, pad2;
@@ -642,21 +643,28 @@ __device__ bool rescan_row_keys(const JacArgs& a, int k, const double* diag, Sh&
     return true;
 }
 
-__device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, Sh& sh) {
-    // eight independent partial sums over eight rows at a time: the loads of
-    // a block overlap and no FMA waits on the previous one
+// This CTA's part of sum_{k<l} a_kl^2 (the strict upper triangle; the
+// matrix is stored in full and symmetric): rows k = rank (mod P), eight rows
+// at a time with eight independent partial sums, so that the loads of a
+// block overlap and no FMA waits on the previous one.  SCALED multiplies
+// every entry by `scale` (a power of two) first, for norms near the ends of
+// the exponent range; otherwise the squares cannot overflow or lose
+// anything that matters and one FMA per entry is enough.
+template <bool SCALED>
+__device__ double upper_offsum_t(const JacArgs& a, int rank, int P, double scale, Sh& sh) {
     double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int k = k0; k < k1; k += 8) {
-        for (int l = threadIdx.x; l < a.n; l += NT) {
+    const int n = a.n;
+    for (int kb = rank; kb < n; kb += 8 * P) {
+        for (int l = ((kb + 1) / NT) * NT + (int)threadIdx.x; l < n; l += NT) {
             double x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int kk = k + u;
-                x[u] = (kk < k1 && kk != l) ? ldcg(a.A + (long long)kk * a.lda + l) : 0.0;
+                const int k = kb + u * P;
+                x[u] = (k < n && l > k) ? ldcg(a.A + (long long)k * a.lda + l) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const double y = __dmul_rn(x[u], scale);
+                const double y = SCALED ? __dmul_rn(x[u], scale) : x[u];
                 acc[u] = __fma_rn(y, y, acc[u]);
             }
         }
@@ -664,6 +672,18 @@ __device__ double owned_offsum(const JacArgs& a, int k0, int k1, double scale, S
     double t = __dadd_rn(__dadd_rn(__dadd_rn(acc[0], acc[1]), __dadd_rn(acc[2], acc[3])),
                          __dadd_rn(__dadd_rn(acc[4], acc[5]), __dadd_rn(acc[6], acc[7])));
     return block_sum(t, sh);
+}
+
+__device__ double upper_offsum(const JacArgs& a, int rank, int P, Sh& sh) {
+    return sh.scaled_sum ? upper_offsum_t<true>(a, rank, P, sh.scale, sh)
+                         : upper_offsum_t<false>(a, rank, P, sh.scale, sh);
+}
+
+// off(A) = sqrt(2 g) from the cluster's sum g of the upper-triangle parts
+__device__ __forceinline__ double off_from_sum(double g, const Sh& sh) {
+    if (!(sh.normf > 0.0)) return 0.0;
+    const double r = sqrt(2.0 * g);
+    return sh.scaled_sum ? __dmul_rn(r, 1.0 / sh.scale) : r;
 }
 
 // Solve one problem.  rank/P: this CTA's rank in the cluster and the
@@ -734,6 +754,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         sh.thr = a.tol * nf;
         sh.eps_li = a.tol * nf / (2.0 * (double)n * (double)(n - 1));
         sh.scale = (nf > 0.0) ? ldexp(1.0, -ilogb(nf)) : 1.0;
+        sh.scaled_sum = !(nf >= 0x1p-300 && nf <= 0x1p300);
         sh.key_eps = value_key(sh.eps_li);
     }
     par ^= 1;
@@ -746,7 +767,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
 
     // ---- convergence test (collective over the cluster) ----
     auto offdiag_check = [&](bool& stop_now) {
-        double part = owned_offsum(a, k0, k1, sh.scale, sh);
+        double part = upper_offsum(a, rank, P, sh);
         if (tid == 0) {
             sh.slots[par].sum = part;
             sh.slots[par].flags = (rank == 0 && a.budget_ns > 0 && (long long)(now_ns() - start) > a.budget_ns) ? 1 : 0;
@@ -755,7 +776,7 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
         if (tid == 0) {
             double g = 0.0;
             for (int r = 0; r < P; ++r) g += peer_slot<CLUSTER>(sh, par, r)->sum;
-            double off = (sh.normf > 0.0) ? __dmul_rn(sqrt(g), 1.0 / sh.scale) : 0.0;
+            const double off = off_from_sum(g, sh);
             int dec = 0;
             if (peer_slot<CLUSTER>(sh, par, 0)->flags & 1) dec = 2;
             else if (a.stop == PJAC_STOP_OFFDIAG && off <= sh.thr) dec = 1;
@@ -1251,13 +1272,13 @@ __device__ void jacobi_problem(const JacArgs& a, int rank, int P, Sh& sh, double
     }
 
     // final off(A) and outputs
-    double part = owned_offsum(a, k0, k1, sh.scale, sh);
+    double part = upper_offsum(a, rank, P, sh);
     if (tid == 0) sh.slots[par].sum = part;
     cta_exchange_sync<CLUSTER>();
     if (tid == 0) {
         double g = 0.0;
         for (int r = 0; r < P; ++r) g += peer_slot<CLUSTER>(sh, par, r)->sum;
-        sh.q = (sh.normf > 0.0) ? __dmul_rn(sqrt(g), 1.0 / sh.scale) : 0.0;
+        sh.q = off_from_sum(g, sh);
     }
     // keep peers' shared memory alive until everyone has read it
     cta_exchange_sync<CLUSTER>();
