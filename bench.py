@@ -62,15 +62,15 @@ FP64_PEAK_SOURCE = "measured by pjac_probe_fp64 on a B300 of this machine (1.199 TF
 
 # DRAM bytes (read + write) of one launch of the Jacobi kernel, from the
 # committed ncu captures, as (one-time bytes, bytes per rotation):
-#   n = 4096: an 8,000-rotation launch moved 6.93 GB; 0.19 GB of it is the
+#   n = 4096: an 8,000-rotation launch moved 6.64 GB; 0.19 GB of it is the
 #             initial scan (A1 read, key matrix written), the rest grows with
 #             the rotations (profiles/jacobi_single_kernel_cfg3_n4096.md);
-#   n = 1024: the working set stays in L2, 19.8 MB for a 30,000-rotation
+#   n = 1024: the working set stays in L2, 18.9 MB for a 30,000-rotation
 #             launch (profiles/jacobi_single_kernel_cfg2_n1024.md).
-JACOBI_DRAM = {4096: (0.19e9, (6.93e9 - 0.19e9) / 8000.0), 1024: (19.8e6, 0.0)}
+JACOBI_DRAM = {4096: (0.19e9, (6.636e9 - 0.19e9) / 8000.0), 1024: (18.9e6, 0.0)}
 JACOBI_TRAFFIC_SOURCE = {
     4096: "ncu dram__bytes_read+write of an 8,000-rotation launch, scaled by rotations (one-time 0.19 GB "
-          "+ 0.84 MB per rotation)",
+          "+ 0.81 MB per rotation)",
     1024: "ncu dram__bytes_read+write of a 30,000-rotation launch (working set in L2)"}
 
 
