@@ -71,6 +71,10 @@ struct pjac_handle {
     // refinement steps of the last solve: order, steps applied, their
     // Newton--Schulz steps in all (for pjac_solve_launch_count)
     int ref_n = 0, ref_done = 0, ref_ns = 0;
+    // set while a solve must not wait on the host (the server's lanes): the
+    // refinement then takes the largest Newton--Schulz count instead of
+    // reading the correction's size back
+    bool no_host_wait = false;
     cudaEvent_t ev[4];
     std::mutex mu;
 };
@@ -365,15 +369,20 @@ static int refine_step(pjac_handle* h, double* A1, long long lda1, double* Q, lo
                        cudaStream_t st) {
     double* E = w.Z;
     CK(refine_build(A1, lda1, n, REFINE_TAU, E, w.maxsum, REFINE_MAX_ROWSUM, st));
-    // the largest absolute row sum of D before scaling: the step count of
-    // the orthogonalisation (one small copy; the solve is not captured)
-    unsigned long long bits = 0;
-    CK(cudaMemcpyAsync(&bits, w.maxsum, sizeof(bits), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    double rowsum = 0.0;
-    std::memcpy(&rowsum, &bits, sizeof(rowsum));
-    const int ns = refine_ns_count(std::min(rowsum, REFINE_MAX_ROWSUM));
-    if (ns == 0) return PJAC_OK;   // D = 0: nothing to refine
+    int ns = REFINE_NS_STEPS;
+    if (!h->no_host_wait) {
+        // the largest absolute row sum of D before scaling: the step count of
+        // the orthogonalisation (one small copy; the solve is not captured)
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, w.maxsum, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double rowsum = 0.0;
+        std::memcpy(&rowsum, &bits, sizeof(rowsum));
+        ns = refine_ns_count(std::min(rowsum, REFINE_MAX_ROWSUM));
+        if (ns == 0) return PJAC_OK;   // D = 0: nothing to refine
+    }
+    // (without the read-back: the largest count, and a zero correction goes
+    // through the steps unchanged, E = 0 staying 0)
     h->ref_done++;
     h->ref_ns += ns;
     int r;
@@ -658,7 +667,11 @@ int solve_async_dev(pjac_handle* h, const double* A, int n, int lda, pjac_pivot 
     SolveWs w;
     r = layout_ws(h, n, &w, st);
     if (r) return r;
+    // nothing in this call waits for the device (the server runs it on the
+    // thread that also admits and polls every other request)
+    h->no_host_wait = true;
     r = solve_pipeline(h, A, n, lda, pivot, tol, W, V, ldv, w, st);
+    h->no_host_wait = false;
     if (r) return r;
     CK(launch_info_single(w.info, dinfo, st));
     return PJAC_OK;
