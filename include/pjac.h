@@ -106,10 +106,14 @@ typedef struct {
      * symmetric eigenproblem: with A1 = diag(d) + E, D_ij = e_ij/(d_j - d_i)
      * for pairs with |e_ij| <= 0.01 |d_j - d_i| (the rest are left to
      * Jacobi), D scaled so its largest absolute row sum is <= 1/4, Z = I + D
-     * made orthogonal by 5 Newton--Schulz steps, then A1 <- Z^T A1 Z,
-     * Q <- Q Z.  Nine working-precision products per step; it resolves the
-     * well-separated pairs on the tensor cores and leaves fewer rotations
-     * to the Jacobi iteration.  0..8. */
+     * made orthogonal by Newton--Schulz steps, then A1 <- Z^T A1 Z,
+     * Q <- Q Z.  The step count is the least k >= 1 with
+     * rho^(2^(k+1)) <= 2^-56 for the row-sum bound rho of the scaled D, at
+     * most 5, read back from the device (a step with D = 0 is skipped); the
+     * serving lanes, which must not wait on the host, take 5.  Two products
+     * per Newton--Schulz step and three more per refinement step; it
+     * resolves the well-separated pairs on the tensor cores and leaves fewer
+     * rotations to the Jacobi iteration.  0..8. */
     int refine_steps;
     /* Most sweeps of the parallel-order FP32 Jacobi pass of the low-precision
      * eigenbasis (it stops earlier once its off-diagonal mass stagnates);
