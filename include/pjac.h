@@ -458,6 +458,21 @@ int pjac_serve_get_stats(pjac_server* s, pjac_serve_stats* st);
  * accounting; returns -1 when h is NULL or n is out of range. */
 int pjac_solve_launch_count(pjac_handle* h, int n);
 
+/* The plan of the split-BF16 product of shape m x n x k (host only; no
+ * device work, no handle): how the digit-slice pairs are scheduled.
+ *   symmetric  1: the plan of pjac_product_symmetric (m == n).
+ *   sms        SMs the plan is made for (0: the current device's count, 148
+ *              when there is none).
+ *   info [out, host, 6 ints] b (bits per digit), S (slices), units (blocks of
+ *              up to 2 x 2 slice pairs sharing their operand tiles), splits
+ *              (CTAs that share one output tile's pairs), CTAs of the
+ *              product kernel, pairs in all (the pairs (s, t) with s + t < S).
+ *   pairs [out, host, nullable] the pairs in launch order as quadruples
+ *              (s, t, unit, split), at most pairs_cap of them.
+ * A diagnostic of the schedule.  PJAC_EINVAL for invalid sizes (every k up
+ * to PJAC_MAX_N has a plan: 5-bit digits reach k = 17458). */
+int pjac_product_plan(int m, int n, int k, int symmetric, int sms, int* info, int* pairs, int pairs_cap);
+
 /* Number of kernel launches of this library that one pjac_product of shape
  * m x n x k makes with the handle's current transform (split BF16: digit
  * split, slice products, reduction when the inner dimension is split; FP64:

@@ -894,6 +894,16 @@ extern "C" int pjac_product_launch_count(pjac_handle* h, int m, int n, int k) {
     return c > 0 ? c : -1;
 }
 
+extern "C" int pjac_product_plan(int m, int n, int k, int symmetric, int sms, int* info, int* pairs,
+                                 int pairs_cap) {
+    if (!info || m < 1 || n < 1 || k < 1 || m > PJAC_MAX_N || n > PJAC_MAX_N || k > PJAC_MAX_N ||
+        (symmetric != 0 && symmetric != 1) || (symmetric && m != n) || pairs_cap < 0 || sms < 0)
+        return set_err(PJAC_EINVAL, "invalid product plan query");
+    if (gemm_split_bf16_plan(m, n, k, symmetric != 0, sms, info, pairs, pairs_cap) != 0)
+        return set_err(PJAC_ENOTIMPL, "split-BF16 product not available for inner dimension %d", k);
+    return PJAC_OK;
+}
+
 extern "C" const char* pjac_status_string(int s) {
     switch (s) {
         case PJAC_OK: return "PJAC_OK";

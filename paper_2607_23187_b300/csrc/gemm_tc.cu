@@ -761,6 +761,35 @@ int gemm_split_bf16_launches(int m, int n, int k, bool sym) {
     return 3 + (L.P.splits > 1 ? 1 : 0);
 }
 
+// The plan of one product (host only): see pjac_product_plan.
+int gemm_split_bf16_plan(int m, int n, int k, bool sym, int sms, int* info, int* pairs, int cap) {
+    Layout L;
+    if (!make_layout(m, n, k, sms > 0 ? sms : device_sms(), L, sym)) return -1;
+    const TcPlan& P = L.P;
+    const int tiles = P.sym ? (P.Np / TN) * (P.Np / TN + 1) / 2 : (P.Mp / TM) * (P.Np / TN);
+    info[0] = P.b;
+    info[1] = P.S;
+    info[2] = P.nunits;
+    info[3] = P.splits;
+    info[4] = tiles * P.splits;
+    int np = 0;
+    for (int z = 0; z < P.splits; ++z)
+        for (int g = P.split_begin[z]; g < P.split_begin[z + 1]; ++g)
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c)
+                    if (unit_pair(P.unit[g], P.S, a, c)) {
+                        if (pairs && np < cap) {
+                            pairs[4 * np + 0] = (P.unit[g] & 255) + a;
+                            pairs[4 * np + 1] = ((P.unit[g] >> 8) & 255) + c;
+                            pairs[4 * np + 2] = g;
+                            pairs[4 * np + 3] = z;
+                        }
+                        ++np;
+                    }
+    info[5] = np;
+    return 0;
+}
+
 // Loads this file's kernels on the current device: asking for a kernel's
 // attributes loads it, where a first launch would otherwise do so later.
 cudaError_t preload_tc_kernels() {

@@ -107,6 +107,9 @@ cudaError_t gemm_split_bf16(bool ta, bool tb, int m, int n, int k, double alpha,
 size_t gemm_split_bf16_ws(int m, int n, int k);          // 0: k too large for the exact split product
 int* gemm_split_bf16_errflag(void* ws);                 // device status word (0 = ok), sticky until cleared
 int gemm_split_bf16_launches(int m, int n, int k, bool sym = false);   // kernel launches per product
+// Host-only plan of a product (info: b, S, units, splits, CTAs, pairs; pairs
+// as (s, t, unit, split) quadruples, at most cap); -1 when k is too large.
+int gemm_split_bf16_plan(int m, int n, int k, bool sym, int sms, int* info, int* pairs, int cap);
 cudaError_t gemm_split_bf16_fold_status(void* ws, DevInfo* info, cudaStream_t st);
 
 // diag32.cu: FP32 parallel-order Jacobi diagonalisation of fl32(A); Q0 out (ld n)

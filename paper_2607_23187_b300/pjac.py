@@ -32,7 +32,7 @@ EXPORTS = (
     "pjac_solve", "pjac_solve_preconditioned", "pjac_solve_batched", "pjac_serve_default_opts",
     "pjac_serve_create", "pjac_serve_destroy", "pjac_serve_submit", "pjac_serve_poll",
     "pjac_serve_progress", "pjac_serve_get_stats", "pjac_status_string", "pjac_last_error",
-    "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_product_symmetric",
+    "pjac_solve_preconditioned_noalloc", "pjac_product", "pjac_product_symmetric", "pjac_product_plan",
     "pjac_solve_launch_count",
     "pjac_product_launch_count", "pjac_eig_lowprec", "pjac_svd", "pjac_svd_onesided", "pjac_probe_fp64",
     "pjac_batched_stage_ms", "pjac_batched_tuning", "pjac_fp32_sweeps_done",
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         L.pjac_svd_onesided.argtypes = [vp, vp, i, i, i, i, d, vp, vp, i, vp, i, ctypes.POINTER(Info), vp]
         L.pjac_probe_fp64.argtypes = [ctypes.POINTER(d), vp]
         L.pjac_probe_fp64.restype = ctypes.c_int
+        L.pjac_product_plan.argtypes = [i, i, i, i, i, vp, vp, i]
+        L.pjac_product_plan.restype = ctypes.c_int
         L.pjac_batched_stage_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         L.pjac_batched_stage_ms.restype = ctypes.c_int
         L.pjac_batched_tuning.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i),
@@ -475,3 +477,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def product_plan(m: int, n: int, k: int, symmetric: bool = False, sms: int = 0) -> Tuple[dict, list]:
+    """The split-BF16 product's schedule (host only): ({b, S, units, splits,
+    ctas, pairs}, [(s, t, unit, split), ...] in launch order)."""
+    info = (ctypes.c_int * 6)()
+    cap = 128
+    pairs = (ctypes.c_int * (4 * cap))()
+    _check(load().pjac_product_plan(int(m), int(n), int(k), 1 if symmetric else 0, int(sms), info, pairs, cap))
+    keys = ("b", "S", "units", "splits", "ctas", "pairs")
+    d = {kk: info[j] for j, kk in enumerate(keys)}
+    return d, [tuple(pairs[4 * j:4 * j + 4]) for j in range(min(d["pairs"], cap))]
