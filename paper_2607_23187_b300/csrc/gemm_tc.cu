@@ -43,6 +43,8 @@
 //                    64-bit integer registers.
 //  tc_reduce_kernel  sums the per-split partial tiles (exactly, as integers)
 //                    when one tile is spread over several CTAs, and scales.
+// A symmetric product (X^T X, X^T A X) computes only the output tiles on and
+// above the diagonal and writes entry (i, j), i <= j, to (i, j) and (j, i).
 // Every mbarrier wait is bounded: on time-out the CTA records an error in the
 // workspace flag, waits (bounded) for its copies and MMAs in flight, frees its
 // TMEM and returns.

@@ -28,7 +28,11 @@
 // of every CTA's part).
 // Scores are ranked by integer keys; entries whose keys are within the tie
 // band are compared on their exact FP64 scores, so the pivot is the exact
-// argmax of the FP64 scores with ties to the smallest (i,j).
+// argmax of the FP64 scores with ties to the smallest (i,j).  The key of
+// every entry is kept in the key matrix K (int32, n x n), updated with the
+// rotated entries, so that a rescan reads keys instead of recomputing them.
+// The convergence test (every check_every rotations) sums the squares of
+// the strict upper triangle, rows taken cyclically by the cluster's CTAs.
 //
 // A is read and written with ld/st.global.cg (L2), because entries of a row
 // are written by several CTAs between cluster barriers.
